@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 MLS-MPM sand substep and its adjoint.
+
+Metric: particle-substeps per second, forward + backward, on 1,048,576
+particles (8 per cell, 64 x 32 x 64-cell bed) on a 128^3 grid with the
+digging skill driving a box shovel (E 3e5, nu 0.25, rho 1800, phi 35 deg,
+dt 5e-5). One step = restore the rollout start state (shovel inserting),
+a recorded forward of S substeps with checkpoints every K, the MSE loss
+against a target cloud and the checkpointed backward to
+dL/d{E, nu, rho, phi, theta}. ``value`` counts N * S particle-substeps per
+step. The forward-only rate is reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the instances shard with no data exchange): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# algorithmic bytes per particle per launch (FP32 state; reads + writes the
+# method needs, grid traffic not counted)
+ALGO_BYTES = {
+    "k_p2g": 96 + 36,          # read x, v, C, F; write F
+    "k_g2p": 12 + 60,          # read x; write x, v, C
+    "k_g2p_bwd": 12 + 60 + 12,  # read x, adj x/v/C; write adj x
+    "k_p2g_bwd": 96 + 48 + 96,  # read state and adj x/F; write adj x/v/C/F
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--substeps", type=int, default=100)
+    ap.add_argument("--checkpoint", type=int, default=50)
+    ap.add_argument("--start", type=int, default=600, help="substep of the rollout start state")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus_id = bus_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands, on a bounded sample
+# --------------------------------------------------------------------------
+def oracle_sample(w, cells: int, nsub: int, start_substep: int):
+    """fwd+bwd of the oracle on the particles of a cells^3 block of the bed,
+    on the workload's own grid; returns (particle-substeps/s, seconds, description)."""
+    import numpy as np
+
+    import oracle
+
+    x0 = w.x0.astype(np.float64)
+    lo = x0.min(0)
+    sel = np.all((x0 - lo) < cells * w.dx, axis=1)
+    x = x0[sel]
+    n = x.shape[0]
+    p = oracle.Params(res=tuple(w.res), dx=w.dx, dt=w.dt, gravity=tuple(w.gravity), bound=w.bound, E=w.E, nu=w.nu,
+                      rho=w.rho, phi_deg=w.phi_deg, vol=w.vol, friction=w.friction, shovel_half=tuple(w.shovel_half))
+    acts, T, _ = oracle.skill_actions(w.traj.theta, w.traj.v_lin, w.traj.v_ang, w.traj.substeps_per_action * w.dt)
+    poses = oracle.pose_table(w.traj.start_pose, acts, w.traj.substeps_per_action, w.dt,
+                              start_substep + nsub)[start_substep:]
+    v, C, F = np.zeros((n, 3)), np.zeros((n, 9)), np.tile(np.eye(3).ravel(), (n, 1))
+    gx = np.full((n, 3), 1.0 / n)
+    t0 = time.perf_counter()
+    st, g = oracle.rollout_adjoint(p, x, v, C, F, poses, gx=gx)
+    dt = time.perf_counter() - t0
+    desc = (f"oracle fwd+bwd (FP64 C, 1 thread): {n} particles ({cells}^3-cell block of the bed) x {nsub} substeps "
+            f"on the {w.res[0]}^3 grid")
+    return n * nsub / dt, dt, desc
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2510_17335_gb300 import workloads as W
+    w = W.cfg_1m()
+    for _ in range(args.warmup):
+        oracle_sample(w, 16, 10, args.start)
+    rates, secs = [], 0.0
+    desc = ""
+    for _ in range(args.steps):
+        r, s, desc = oracle_sample(w, 16, 10, args.start)
+        rates.append(r)
+        secs += s
+    value = sum(rates) / len(rates)
+    line = {"metric": "particle-substeps/s (fwd+bwd)", "value": value, "unit": "particle-substeps/s",
+            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "bed1m_grid128 (sampled block)", "particles": w.n, "grid": list(w.res)},
+            "cpu_baseline": {"value": value, "unit": "particle-substeps/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "particle-substeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our implementation
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2510_17335_gb300 import mpm
+    from paper_2510_17335_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = W.cfg_1m()
+    N, S, K = w.n, args.substeps, args.checkpoint
+    stream = torch.cuda.Stream()
+    opts = mpm.make_options(checkpoint_every=K)
+    sim = mpm.simulation_from_workloads([w], opts)
+    sim.set_stream(stream.cuda_stream)
+    dev = torch.device("cuda", local)
+    with torch.cuda.stream(stream):
+        # rollout start state: the skill at substep `start` (shovel inserting)
+        sim.forward(args.start)
+        st0 = {k: torch.empty((N, 3) if k in "xv" else (N, 3, 3), device=dev) for k in "xvCF"}
+        sim.get_state(device_out=st0)
+        target = (torch.from_numpy(w.x0).to(dev) + torch.tensor([0.003, -0.002, 0.001], device=dev)).contiguous()
+        dldx = torch.empty((N, 3), device=dev)
+    stream.synchronize()
+
+    def step():
+        sim.set_substep(args.start)
+        sim.set_state(st0["x"], st0["v"], st0["C"], st0["F"])
+        sim.forward(S, record=True)
+        sim.loss_mse(target, grad_out=dldx)
+        return sim.backward(dL_dx=dldx)
+
+    def fwd_step():
+        sim.set_substep(args.start)
+        sim.set_state(st0["x"], st0["v"], st0["C"], st0["F"])
+        sim.forward(S)
+
+    bus = None
+    try:
+        pr = torch.cuda.get_device_properties(local)
+        bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+    except Exception:
+        bus = None
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+            fwd_step()
+        # ---- timed: forward + backward ----
+        launches0 = sim.info()["kernel_launches"]
+        sim.profile(True)
+        clocks = ClockSampler(bus)
+        clocks.start()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            grads = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        prof = sim.profile_read()
+        sim.profile(False)
+        launches = sim.info()["kernel_launches"] - launches0
+        ms = e0.elapsed_time(e1)
+        # ---- forward only ----
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            fwd_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1)
+
+    t = torch.tensor([ms, fms], device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, fms = float(t[0]), float(t[1])
+    value = ws * N * S * args.steps / (ms / 1e3)
+    fwd_value = ws * N * S * args.steps / (fms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty((N, 3), dtype=torch.float32, pin_memory=True)
+        xh.copy_(st0["x"].cpu())
+        vh = torch.empty((N, 3), dtype=torch.float32, pin_memory=True); vh.copy_(st0["v"].cpu())
+        Ch = torch.empty((N, 3, 3), dtype=torch.float32, pin_memory=True); Ch.copy_(st0["C"].cpu())
+        Fh = torch.empty((N, 3, 3), dtype=torch.float32, pin_memory=True); Fh.copy_(st0["F"].cpu())
+        th = torch.empty((N, 3), dtype=torch.float32, pin_memory=True); th.copy_(target.cpu())
+        arrs = [a.numpy() for a in (xh, vh, Ch, Fh, th)]
+
+        def e2e_step():
+            sim.set_substep(args.start)
+            sim.set_state(*arrs[:4])
+            sim.forward(S, record=True)
+            L, g = sim.loss_mse(arrs[4])
+            return sim.backward(dL_dx=g)
+
+        with torch.cuda.stream(stream):
+            e2e_step()
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                gm, gt = e2e_step()
+            torch.cuda.synchronize()
+            barrier()
+            es = time.perf_counter() - t0
+        te = torch.tensor([es], device=dev)
+        if dist is not None:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        h2d = N * 4 * (3 + 3 + 9 + 9) + 2 * N * 3 * 4      # state, target and dL/dx in
+        d2h = N * 3 * 4 + 8 * (1 + 4 + 6)                   # dL/dx, loss and gradients out
+        e2e = {"value": ws * N * S * args.steps / float(te[0]), "unit": "particle-substeps/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (largest summed device time)
+    peak, peak_kind = measured_peaks()
+    name = max(prof, key=lambda k: prof[k][0])
+    tot_ms, nl = prof[name]
+    avg_s = tot_ms / 1e3 / max(nl, 1)
+    kernels = {k: {"ms_total": round(v[0], 3), "launches": v[1],
+                   "share": round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)} for k, v in prof.items()}
+    roof = None
+    if name in ALGO_BYTES:
+        algo = ALGO_BYTES[name] * N
+        ach = algo / avg_s / 1e9
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "dram_traffic.json")
+        if os.path.exists(tf):
+            try:
+                d = json.load(open(tf))
+                ent = d.get(name)
+                if ent and ent.get("kernel_source_sha") == kernel_source_sha():
+                    traffic = ent["dram_bytes_per_launch_full_size"]
+            except Exception:
+                traffic = None
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": traffic, "kernel": name, "algo_bytes_per_launch": algo,
+                "avg_launch_us": round(avg_s * 1e6, 2), "peak_kind": f"{peak_kind} hbm_gbs"}
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        r, secs, desc = oracle_sample(w, 24, 16, args.start)
+        cpu = {"value": r, "unit": "particle-substeps/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": round(secs, 2)}
+    line = {
+        "metric": "particle-substeps/s (fwd+bwd)", "value": value, "unit": "particle-substeps/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "bed1m_grid128: 1,048,576 particles, 128^3 grid, skill-driven box shovel",
+                   "substeps_per_step": S, "checkpoint_every": K, "start_substep": args.start,
+                   "l2": "inputs larger than L2 (96 MB state + 4.9 GB segment buffers per step)",
+                   "parallelism": f"replicas x{ws}"},
+        "fwd_value": fwd_value, "fwd_ms_per_step": fms / args.steps,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "kernels": kernels, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def kernel_source_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("mpm_kernels.cu", "mpm_device.cuh", "mpm_types.h"):
+        h.update(open(os.path.join(ROOT, "paper_2510_17335_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    from paper_2510_17335_gb300 import build
+    build.build()
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

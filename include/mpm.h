@@ -1,0 +1,204 @@
+/*
+ * mpm.h -- C ABI of the GB300 (sm_103a) MLS-MPM sand/soil substep and its
+ * reverse-mode adjoint, after DDBot (arXiv 2510.17335).
+ *
+ * What one substep computes (Sec. III-A, Algorithm 1; Eqs. (3)-(7)):
+ *   per particle: trial F = (I + dt C) F; SVD; Drucker-Prager return of the
+ *   singular values (Eqs. (6)-(7)); F' = U S^ V^T; Kirchhoff stress
+ *   tau = P' F'^T of the SVK log-strain energy (Eqs. (3)-(4), det F' := 1);
+ *   APIC/MLS-MPM scatter of mass and momentum with quadratic B-splines;
+ *   per grid node: v = mv/m + dt g, slip walls, box-shovel SDF contact with
+ *   Coulomb friction; per particle: APIC gather of v and C, the same shovel
+ *   contact on the particle velocity, x += dt v.
+ * The adjoint (Sec. III-D; Appendix B) is the exact reverse of that substep,
+ * chained over a rollout with checkpointing, and yields dL/d{E, nu, rho,
+ * phi} and dL/d(the six skill parameters) through the skill-to-action map
+ * (Sec. III-B, Algorithm 2, rounded phase lengths).
+ *
+ * Conventions
+ *   - y is up. Instance domains are [0, res_k * dx) per axis; node (i,j,k)
+ *     sits at (i,j,k) * dx. A particle must stay in [dx, (res_k - 2) dx);
+ *     leaving it is reported as MPM_ERR_OUT_OF_DOMAIN.
+ *   - Particle arrays crossing this boundary are FP32, in "external order":
+ *     the instances one after another, each in its own creation order, with
+ *     no padding. Positions/velocities are 3 floats per particle, C and F 9
+ *     floats per particle (row-major 3x3), interleaved per particle
+ *     (x[3*p + k]).
+ *   - A shovel pose is (tip x, y, z, tilt psi). The box spans local
+ *     x in [-hx, hx], y in [0, 2 hy], z in [-hz, hz] above the tip, rotated
+ *     by R(psi) = [[cos, sin, 0], [-sin, cos, 0], [0, 0, 1]] about the tip;
+ *     psi tilts the pointing direction to (-sin psi, -cos psi, 0).
+ *   - Actions are per global step, 6 doubles in the simulator frame
+ *     [dx, dy, dz, dpsi, 0, 0]; each step's displacement is split evenly
+ *     over its substeps (Sec. III-A, actions). Components 4 and 5 must be 0.
+ *   - `device_ptrs` = 1 means the float pointers are CUDA device pointers
+ *     (read/written on the handle's stream); 0 means host pointers (the call
+ *     copies and synchronises).
+ *   - Ownership: the library allocates and owns all of its device memory;
+ *     inputs are copied in; outputs are written into caller buffers. A
+ *     handle must not be used from two threads at once.
+ *   - Errors: every int-returning call returns MPM_OK (0) or a negative
+ *     code; no exception crosses the boundary. Device-side errors (domain,
+ *     non-finite values) are collected in a status word and reported by the
+ *     call that ran the kernels.
+ */
+#ifndef MPM_GB300_H
+#define MPM_GB300_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPM_OK 0
+#define MPM_ERR_INVALID_ARG (-1)  /* bad size, parameter out of range, NULL where required */
+#define MPM_ERR_OOM (-2)          /* device allocation failed */
+#define MPM_ERR_CUDA (-3)         /* a CUDA call failed */
+#define MPM_ERR_OUT_OF_DOMAIN (-4)/* a particle left [dx, (res-2) dx) */
+#define MPM_ERR_NON_FINITE (-5)   /* NaN/Inf in the state or an adjoint */
+#define MPM_ERR_NO_RECORD (-6)    /* backward without a recorded forward */
+#define MPM_ERR_TIMEOUT (-7)      /* a bounded device wait gave up */
+#define MPM_ERR_NO_DEVICE (-8)    /* no usable sm_103 device */
+
+typedef struct mpm_handle mpm_handle;
+
+/* Material of one instance, Theta in Sec. III-A; E in Pa (the paper's table
+ * prints a kPa header over Pa values), nu in (0, 0.5), rho in kg/m^3,
+ * phi_deg (friction angle) in (0, 90). */
+typedef struct {
+    double E, nu, rho, phi_deg;
+} mpm_material;
+
+/* Grid and contact setup of one instance. */
+typedef struct {
+    int res[3];               /* grid nodes per axis, each in [8, 1024] */
+    double dx;                /* node spacing (> 0) */
+    double dt;                /* substep (> 0) */
+    double gravity[3];        /* m/s^2 */
+    int bound;                /* wall layer thickness in nodes (>= 0) */
+    double particle_volume;   /* V_p; the particle mass is rho * V_p */
+    double friction;          /* Coulomb coefficient of the shovel contact */
+    int particle_collision;   /* 1: apply the shovel contact to particles too */
+    double shovel_half[3];    /* box half extents (x thickness, y length, z width) */
+    int shovel_on;            /* 0: no shovel */
+} mpm_config;
+
+/* Handle-wide options; pass NULL for the defaults in brackets. */
+typedef struct {
+    int checkpoint_every;     /* [50] substeps per checkpoint segment */
+    int clip_grads;           /* [0] clip adjoints of x, v, F and of grid m, v, v' (Sec. III-E) */
+    double clip_value;        /* [1e4] */
+    double sigma_min;         /* [1e-4] singular values are clamped here before the log */
+    int sort_every;           /* [0] reorder particles by grid block every n substeps (0: never) */
+} mpm_options;
+
+/* Digging skill (Sec. III-B): theta = (displace, rotate, insert_dist,
+ * push_angle, push_dist, lift) in [-1, 1]; lift sets d4 = (lift + 1) 0.005 m
+ * (lift = 1 is the paper's 0.01 m). The global step is
+ * substeps_per_action * dt. */
+typedef struct {
+    double theta[6];
+    double v_lin, v_ang;      /* end-effector speeds (m/s, rad/s), > 0 */
+    int substeps_per_action;  /* N >= 1 */
+    double start_pose[4];     /* tip x, y, z, psi */
+} mpm_skill;
+
+typedef struct {
+    int n_inst;
+    int64_t n_particles;      /* total over instances */
+    int64_t substep;          /* substeps run since create/reset */
+    int64_t recorded;         /* substeps recorded for backward (0 if none) */
+    int64_t device_bytes;     /* device memory held */
+    int64_t kernel_launches;  /* kernels launched by the library so far */
+    int64_t fp64_fallbacks;   /* constitutive evaluations redone in FP64 */
+} mpm_info_t;
+
+/* Create a batch of n_inst independent instances. cfgs/mats have n_inst
+ * entries; counts[i] particles of instance i (>= 0); x0 holds the initial
+ * positions in external order (host pointer, sum(counts) * 3 floats). The
+ * initial state is v = 0, C = 0, F = I. Runs on the current CUDA device. */
+int mpm_create(int n_inst, const mpm_config* cfgs, const mpm_material* mats, const int64_t* counts,
+               const float* x0, const mpm_options* opts, mpm_handle** out);
+
+/* Replace the material of one instance (takes effect at the next call). */
+int mpm_set_material(mpm_handle* h, int inst, const mpm_material* mat);
+
+/* Scripted shovel motion: start pose and n_actions actions (host,
+ * n_actions * 6 doubles). After the last action the shovel rests. */
+int mpm_set_shovel_actions(mpm_handle* h, int inst, const double start_pose[4], int n_actions,
+                           const double* actions, int substeps_per_action);
+
+/* Skill-driven shovel motion: Algorithm 2 maps theta to actions; backward
+ * then also returns dL/dtheta through the Jacobian with frozen T_i. */
+int mpm_set_shovel_trajectory(mpm_handle* h, int inst, const mpm_skill* skill);
+
+/* Number of actions of an instance's current trajectory (>= 0), or < 0. */
+int mpm_num_actions(mpm_handle* h, int inst);
+
+/* Back to the creation state (x0, v = 0, C = 0, F = I), substep 0, no record. */
+int mpm_reset(mpm_handle* h);
+
+/* Overwrite the current state (all instances, external order). NULL v/C/F
+ * mean 0, 0 and I. Drops any record. */
+int mpm_set_state(mpm_handle* h, const float* x, const float* v, const float* C, const float* F,
+                  int device_ptrs);
+
+/* Read the current state (any output may be NULL). */
+int mpm_get_state(mpm_handle* h, float* x, float* v, float* C, float* F, int device_ptrs);
+
+/* Advance all instances by n_substeps (>= 0). record = 1 keeps what the
+ * backward needs: one state checkpoint every checkpoint_every substeps (the
+ * backward recomputes each segment). A recording forward continues an
+ * existing record only if the previous call recorded too. */
+int mpm_forward(mpm_handle* h, int n_substeps, int record);
+
+/* L_i = (1/N_i) sum_p |x_p - xhat_p|^2 per instance (FP64 accumulation) and,
+ * if dL_dx != NULL, dL/dx = 2 (x - xhat) / N_i (external order). */
+int mpm_loss_mse(mpm_handle* h, const float* x_target, double* loss, float* dL_dx, int device_ptrs);
+
+/* Reverse the recorded rollout. dL_dx / dL_dv: adjoints of the final
+ * positions / velocities (external order; either may be NULL = 0).
+ * dL_dmaterial: n_inst * 4 doubles (E, nu, rho, phi_deg). dL_dtheta:
+ * n_inst * 6 doubles (zero for scripted trajectories), may be NULL.
+ * The record is consumed. */
+int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, int device_ptrs,
+                 double* dL_dmaterial, double* dL_dtheta);
+
+/* After mpm_backward: dL/d(initial state of the recorded rollout). */
+int mpm_get_state_grad(mpm_handle* h, float* gx, float* gv, float* gC, float* gF, int device_ptrs);
+
+/* After mpm_backward: dL/d(actions) of one instance (n_actions * 6 doubles)
+ * and dL/d(start pose) (4 doubles, may be NULL). */
+int mpm_get_action_grad(mpm_handle* h, int inst, double* dL_dactions, double* dL_dstart);
+
+/* Diagnostic: total grid mass per instance (n_inst doubles) after the last
+ * forward substep's P2G; by the partition of unity of the B-spline weights
+ * (Sec. III-A, MLS-MPM transfer) it equals sum_p rho V_p up to rounding. */
+int mpm_grid_mass(mpm_handle* h, double* mass);
+
+/* Set the substep counter (the index into the shovel pose tables) of the
+ * next forward substep; drops any record. */
+int mpm_set_substep(mpm_handle* h, int64_t substep);
+
+/* Kernel timing: enable != 0 records a CUDA event pair around every kernel
+ * launch on the handle's stream (counters reset on every call). Kernel ids:
+ * 0 k_p2g, 1 k_grid, 2 k_g2p, 3 k_g2p_bwd, 4 k_grid_bwd, 5 k_p2g_bwd,
+ * 6 k_grid_clear. mpm_profile_read waits for the recorded events and gives
+ * the summed device time (ms) and the launch count of one kernel. */
+int mpm_profile(mpm_handle* h, int enable);
+int mpm_profile_read(mpm_handle* h, int kernel, double* total_ms, int64_t* launches);
+const char* mpm_kernel_name(int kernel);
+
+/* Run on this CUDA stream (a cudaStream_t; NULL = the legacy default). */
+int mpm_set_stream(mpm_handle* h, void* stream);
+
+int mpm_synchronize(mpm_handle* h);
+int mpm_get_info(mpm_handle* h, mpm_info_t* out);
+void mpm_destroy(mpm_handle* h);
+const char* mpm_error_string(int code);
+int mpm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

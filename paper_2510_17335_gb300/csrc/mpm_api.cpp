@@ -1,0 +1,1017 @@
+// C ABI of the GB300 MLS-MPM sand substep library (see include/mpm.h).
+//
+// Host side: handle and device memory, the skill-to-action mapping of
+// DDBot's Algorithm 2 (Sec. III-B) with its Jacobian, the per-substep shovel
+// pose tables (Sec. III-A, actions), the checkpointed rollout driver and the
+// chain from per-substep adjoints to dL/d{E, nu, rho, phi} and dL/dtheta.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mpm.h"
+#include "mpm_launch.h"
+#include "mpm_types.h"
+
+using namespace mpm;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct Instance {
+    mpm_config cfg;
+    mpm_material mat;
+    int64_t n = 0;
+    int64_t ext_off = 0;
+    long long pbeg = 0;
+    int n_chunks = 0;
+    int nb[3] = {0, 0, 0};
+    long long node_off = 0;
+    int blk_off = 0;
+    int n_blocks = 0;
+    // trajectory
+    bool has_traj = false;
+    bool has_skill = false;
+    mpm_skill skill;
+    double start[4] = {0, 0, 0, 0};
+    int spa = 1;                      // substeps per action
+    std::vector<double> actions;      // n_actions * 6
+    std::vector<double> jac;          // n_actions * 36 (skill only)
+    long long pose_off = 0;           // offset (floats) into the pose buffer
+    int n_poses = 0;
+    // results of the last backward
+    std::vector<double> gactions;
+    double gstart[4] = {0, 0, 0, 0};
+};
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    int ensure(size_t count, int64_t& total) {
+        if (count <= n) return MPM_OK;
+        release();
+        if (count == 0) return MPM_OK;
+        if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return MPM_ERR_OOM;
+        }
+        total += (int64_t)((count - n) * sizeof(T));
+        n = count;
+        return MPM_OK;
+    }
+};
+
+// CUDA-event timing of every kernel launch (on the launching stream),
+// switched on by mpm_profile()
+struct Profiler {
+    bool on = false;
+    struct Pending {
+        int id;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    double total_ms[(int)KernelId::Count] = {0};
+    int64_t count[(int)KernelId::Count] = {0};
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void flush() {
+        for (auto& p : pending) {
+            cudaEventSynchronize(p.b);
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                total_ms[p.id] += ms;
+                count[p.id] += 1;
+            }
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+        cudaGetLastError();
+    }
+    void reset() {
+        flush();
+        for (int i = 0; i < (int)KernelId::Count; i++) {
+            total_ms[i] = 0.0;
+            count[i] = 0;
+        }
+    }
+    void release() {
+        flush();
+        for (auto e : pool) cudaEventDestroy(e);
+        pool.clear();
+    }
+};
+
+}  // namespace
+
+struct mpm_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    mpm_options opt;
+    std::vector<Instance> inst;
+    int64_t n_ext = 0;
+    long long ncap = 0;
+    int n_chunks = 0;
+    int n_blocks = 0;
+    long long n_nodes = 0;
+    int64_t device_bytes = 0;
+    int64_t launches = 0;
+
+    DevBuf<InstDev> d_inst;
+    DevBuf<int> d_chunk_inst, d_block_inst, d_ext_of_slot;
+    DevBuf<float> d_state, d_x0, d_stage, d_poses, d_target;
+    DevBuf<float4> d_acc, d_vout;
+    DevBuf<unsigned char> d_flags;
+    DevBuf<int> d_status;
+    DevBuf<unsigned long long> d_fp64;
+    DevBuf<double> d_loss;
+
+    // record / backward
+    int64_t substep = 0;
+    bool recording = false;
+    int64_t rec_start = 0, rec_len = 0;
+    std::vector<DevBuf<float>> ckpt;
+    DevBuf<float> d_seg_state;
+    DevBuf<float4> d_seg_acc, d_seg_vout, d_gacc;
+    DevBuf<unsigned char> d_seg_flags;
+    DevBuf<float> d_adj;
+    DevBuf<double> d_gmat, d_gpose;
+    bool have_grad = false;
+    bool seg_grids_clean = true;
+    Profiler prof;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return MPM_OK;
+    if (e == cudaErrorMemoryAllocation) return MPM_ERR_OOM;
+    return MPM_ERR_CUDA;
+}
+
+#define CK(x)                                 \
+    do {                                      \
+        cudaError_t e__ = (x);                \
+        if (e__ != cudaSuccess) {             \
+            cudaGetLastError();               \
+            return cuda_err(e__);             \
+        }                                     \
+    } while (0)
+
+#define RK(x)                          \
+    do {                               \
+        int r__ = (x);                 \
+        if (r__ != MPM_OK) return r__; \
+    } while (0)
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
+
+int validate_config(const mpm_config& c) {
+    for (int k = 0; k < 3; k++)
+        if (c.res[k] < 8 || c.res[k] > 1024) return MPM_ERR_INVALID_ARG;
+    if (!finite_pos(c.dx) || !finite_pos(c.dt) || !finite_pos(c.particle_volume)) return MPM_ERR_INVALID_ARG;
+    if (c.bound < 0 || c.bound > 16) return MPM_ERR_INVALID_ARG;
+    if (!std::isfinite(c.friction) || c.friction < 0) return MPM_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; k++) {
+        if (!std::isfinite(c.gravity[k])) return MPM_ERR_INVALID_ARG;
+        if (c.shovel_on && !finite_pos(c.shovel_half[k])) return MPM_ERR_INVALID_ARG;
+    }
+    return MPM_OK;
+}
+
+int validate_material(const mpm_material& m) {
+    if (!finite_pos(m.E) || !finite_pos(m.rho)) return MPM_ERR_INVALID_ARG;
+    if (!(m.nu > 0 && m.nu < 0.5)) return MPM_ERR_INVALID_ARG;
+    if (!(m.phi_deg > 0 && m.phi_deg < 90)) return MPM_ERR_INVALID_ARG;
+    return MPM_OK;
+}
+
+// Lame constants (Sec. III-A, Eq. (5)) and the Drucker-Prager coefficient
+// alpha_f (Eq. (6)); beta = (3 lambda + 2 mu) / (2 mu) alpha_f.
+struct Lame {
+    double mu, lam, alpha, beta;
+};
+Lame lame_of(const mpm_material& m) {
+    Lame L;
+    L.mu = m.E / (2.0 * (1.0 + m.nu));
+    L.lam = m.E * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu));
+    const double s = std::sin(m.phi_deg * kPi / 180.0);
+    L.alpha = std::sqrt(2.0 / 3.0) * 2.0 * s / (3.0 - s);
+    L.beta = (3.0 * L.lam + 2.0 * L.mu) / (2.0 * L.mu) * L.alpha;
+    return L;
+}
+
+InstDev make_instdev(const mpm_handle* h, const Instance& I) {
+    InstDev d;
+    std::memset(&d, 0, sizeof d);
+    for (int k = 0; k < 3; k++) {
+        d.res[k] = I.cfg.res[k];
+        d.nb[k] = I.nb[k];
+        d.g[k] = (float)I.cfg.gravity[k];
+        d.sh[k] = (float)I.cfg.shovel_half[k];
+    }
+    d.bound = I.cfg.bound;
+    d.shovel_on = I.cfg.shovel_on;
+    d.pcoll = I.cfg.particle_collision;
+    d.n_poses = I.n_poses;
+    d.n = (int)I.n;
+    d.blk_off = I.blk_off;
+    d.pbeg = I.pbeg;
+    d.node_off = I.node_off;
+    d.dx = (float)I.cfg.dx;
+    d.inv_dx = (float)(1.0 / I.cfg.dx);
+    d.dt = (float)I.cfg.dt;
+    const Lame L = lame_of(I.mat);
+    d.mu = (float)L.mu;
+    d.lam = (float)L.lam;
+    d.alpha = (float)L.alpha;
+    d.beta = (float)L.beta;
+    d.mp = (float)(I.mat.rho * I.cfg.particle_volume);
+    d.vol = (float)I.cfg.particle_volume;
+    d.stress_scale = (float)(-I.cfg.dt * I.cfg.particle_volume * 4.0 / (I.cfg.dx * I.cfg.dx));
+    d.friction = (float)I.cfg.friction;
+    d.smin = (float)h->opt.sigma_min;
+    d.poses = I.n_poses > 0 ? h->d_poses.p + I.pose_off : nullptr;
+    return d;
+}
+
+int upload_instances(mpm_handle* h) {
+    std::vector<InstDev> v;
+    for (auto& I : h->inst) v.push_back(make_instdev(h, I));
+    CK(cudaMemcpyAsync(h->d_inst.p, v.data(), v.size() * sizeof(InstDev), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPM_OK;
+}
+
+// Algorithm 2 (Sec. III-B) with rounded phase lengths, in the simulator
+// frame: the paper's x stays x, its vertical z becomes y, its rx is the tilt
+// psi. jac[t*36 + k*6 + j] = d a_t[k] / d theta_j with T_i frozen.
+int skill_to_actions(const mpm_skill& s, double dt_step, std::vector<double>& act, std::vector<double>& jac) {
+    const double* th = s.theta;
+    const double vl = s.v_lin * dt_step, vw = s.v_ang * dt_step;
+    // phase 1: displace along x and tilt
+    const double d1 = 0.12 * th[0], phi1 = th[1] * kPi / 3.0;
+    const double tp1 = std::fabs(phi1 / vw);
+    const long T1 = std::lround(std::max(std::fabs(d1 / vl), tp1));
+    // phase 2: insert along the tilted pointing direction
+    const double d2 = 0.03 * (th[2] + 1.0), phi2 = phi1 + kPi / 2.0;
+    const long T2 = std::lround(d2 / vl);
+    // phase 3: push along the push angle
+    const double d3 = 0.1 * (th[4] + 1.0) + 0.04, phi3 = (th[3] + 3.0) * kPi / 3.0;
+    const long T3 = std::lround(std::fabs(d3 / vl));
+    // phase 4: untilt and lift
+    const double d4 = 0.005 * (th[5] + 1.0);
+    const long T4 = std::lround(std::max(tp1, d4 / vl));
+    const long T = T1 + T2 + T3 + T4;
+    if (T < 0 || T > 10000000) return MPM_ERR_INVALID_ARG;
+    act.assign((size_t)T * 6, 0.0);
+    jac.assign((size_t)T * 36, 0.0);
+    const double c2 = std::cos(phi2), s2 = std::sin(phi2), c3 = std::cos(phi3), s3 = std::sin(phi3);
+    for (long t = 0; t < T; t++) {
+        double* a = &act[(size_t)t * 6];
+        double* J = &jac[(size_t)t * 36];
+        if (t < T1) {
+            a[0] = d1 / T1;
+            a[3] = phi1 / T1;
+            J[0 * 6 + 0] = 0.12 / T1;
+            J[3 * 6 + 1] = (kPi / 3.0) / T1;
+        } else if (t < T1 + T2) {
+            a[0] = d2 * c2 / T2;
+            a[1] = -d2 * s2 / T2;
+            J[0 * 6 + 2] = 0.03 * c2 / T2;
+            J[1 * 6 + 2] = -0.03 * s2 / T2;
+            J[0 * 6 + 1] = -d2 * s2 * (kPi / 3.0) / T2;
+            J[1 * 6 + 1] = -d2 * c2 * (kPi / 3.0) / T2;
+        } else if (t < T1 + T2 + T3) {
+            a[0] = d3 * c3 / T3;
+            a[1] = d3 * s3 / T3;
+            J[0 * 6 + 4] = 0.1 * c3 / T3;
+            J[1 * 6 + 4] = 0.1 * s3 / T3;
+            J[0 * 6 + 3] = -d3 * s3 * (kPi / 3.0) / T3;
+            J[1 * 6 + 3] = d3 * c3 * (kPi / 3.0) / T3;
+        } else {
+            a[1] = d4 / T4;
+            a[3] = -phi1 / T4;
+            J[1 * 6 + 5] = 0.005 / T4;
+            J[3 * 6 + 1] = -(kPi / 3.0) / T4;
+        }
+    }
+    return MPM_OK;
+}
+
+// Per-substep pose table: each global step's action is spread evenly over
+// its substeps and added to the pose; the velocity is that increment / dt.
+void pose_table(const Instance& I, std::vector<float>& out) {
+    const int na = (int)(I.actions.size() / 6);
+    const int n = std::max(1, na * I.spa);
+    out.assign((size_t)n * 8, 0.0f);
+    double cur[4] = {I.start[0], I.start[1], I.start[2], I.start[3]};
+    for (int s = 0; s < n; s++) {
+        const int t = s / I.spa;
+        double inc[4] = {0, 0, 0, 0};
+        if (t < na)
+            for (int k = 0; k < 4; k++) inc[k] = I.actions[(size_t)t * 6 + k] / I.spa;
+        for (int k = 0; k < 4; k++) {
+            cur[k] += inc[k];
+            out[(size_t)s * 8 + k] = (float)cur[k];
+            out[(size_t)s * 8 + 4 + k] = (float)(inc[k] / I.cfg.dt);
+        }
+    }
+}
+
+int upload_poses(mpm_handle* h) {
+    std::vector<std::vector<float>> tabs(h->inst.size());
+    long long total = 0;
+    for (size_t i = 0; i < h->inst.size(); i++) {
+        Instance& I = h->inst[i];
+        if (I.has_traj) pose_table(I, tabs[i]);
+        I.pose_off = total;
+        I.n_poses = (int)(tabs[i].size() / 8);
+        total += (long long)tabs[i].size();
+    }
+    RK(h->d_poses.ensure((size_t)std::max(total, 8LL), h->device_bytes));
+    for (size_t i = 0; i < h->inst.size(); i++)
+        if (!tabs[i].empty())
+            CK(cudaMemcpyAsync(h->d_poses.p + h->inst[i].pose_off, tabs[i].data(), tabs[i].size() * sizeof(float),
+                               cudaMemcpyHostToDevice, h->stream));
+    return upload_instances(h);
+}
+
+StepArgs base_args(mpm_handle* h) {
+    StepArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.inst = h->d_inst.p;
+    a.chunk_inst = h->d_chunk_inst.p;
+    a.block_inst = h->d_block_inst.p;
+    a.ncap = h->ncap;
+    a.n_chunks = h->n_chunks;
+    a.n_blocks = h->n_blocks;
+    a.status = h->d_status.p;
+    a.fp64_count = h->d_fp64.p;
+    a.clip = h->opt.clip_grads ? (float)h->opt.clip_value : 0.0f;
+    return a;
+}
+
+int read_status(mpm_handle* h) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, h->d_status.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->prof.on) h->prof.flush();
+    if (st) {
+        CK(cudaMemsetAsync(h->d_status.p, 0, sizeof(int), h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    if (st & kStatusNonFinite) return MPM_ERR_NON_FINITE;
+    if (st & kStatusDomain) return MPM_ERR_OUT_OF_DOMAIN;
+    return MPM_OK;
+}
+
+int check_inst(mpm_handle* h, int inst) {
+    if (!h || inst < 0 || inst >= (int)h->inst.size()) return MPM_ERR_INVALID_ARG;
+    return MPM_OK;
+}
+
+int set_device(mpm_handle* h) {
+    CK(cudaSetDevice(h->device));
+    return MPM_OK;
+}
+
+int ensure_stage(mpm_handle* h) { return h->d_stage.ensure((size_t)std::max<int64_t>(h->n_ext, 1) * 24, h->device_bytes); }
+
+int run_kernel(mpm_handle* h, KernelId id, const AdjArgs& A) {
+    if (h->prof.on) {
+        Profiler::Pending p{(int)id, h->prof.get(), h->prof.get()};
+        CK(cudaEventRecord(p.a, h->stream));
+        CK(launch_kernel(id, A, h->stream));
+        CK(cudaEventRecord(p.b, h->stream));
+        h->prof.pending.push_back(p);
+        if (h->prof.pending.size() > 65536) h->prof.flush();
+    } else {
+        CK(launch_kernel(id, A, h->stream));
+    }
+    h->launches++;
+    return MPM_OK;
+}
+
+int run_substep(mpm_handle* h, const StepArgs& a) {
+    AdjArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.f = a;
+    RK(run_kernel(h, KernelId::P2G, A));
+    RK(run_kernel(h, KernelId::Grid, A));
+    RK(run_kernel(h, KernelId::G2P, A));
+    return MPM_OK;
+}
+
+int run_adjoint_substep(mpm_handle* h, const AdjArgs& A) {
+    RK(run_kernel(h, KernelId::G2PBwd, A));
+    RK(run_kernel(h, KernelId::GridBwd, A));
+    RK(run_kernel(h, KernelId::P2GBwd, A));
+    RK(run_kernel(h, KernelId::GridClear, A));
+    return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpm_version(void) { return 1; }
+
+const char* mpm_error_string(int code) {
+    switch (code) {
+        case MPM_OK: return "ok";
+        case MPM_ERR_INVALID_ARG: return "invalid argument";
+        case MPM_ERR_OOM: return "out of device memory";
+        case MPM_ERR_CUDA: return "CUDA error";
+        case MPM_ERR_OUT_OF_DOMAIN: return "a particle left the valid domain [dx, (res-2) dx)";
+        case MPM_ERR_NON_FINITE: return "non-finite value in the state or an adjoint";
+        case MPM_ERR_NO_RECORD: return "backward without a recorded forward";
+        case MPM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case MPM_ERR_NO_DEVICE: return "no usable CUDA device";
+        default: return "unknown error";
+    }
+}
+
+int mpm_create(int n_inst, const mpm_config* cfgs, const mpm_material* mats, const int64_t* counts,
+               const float* x0, const mpm_options* opts, mpm_handle** out) {
+    if (!out) return MPM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_inst < 1 || n_inst > 65536 || !cfgs || !mats || !counts) return MPM_ERR_INVALID_ARG;
+    int64_t n_ext = 0;
+    for (int i = 0; i < n_inst; i++) {
+        RK(validate_config(cfgs[i]));
+        RK(validate_material(mats[i]));
+        if (counts[i] < 0 || counts[i] > (1LL << 30)) return MPM_ERR_INVALID_ARG;
+        n_ext += counts[i];
+    }
+    if (n_ext > 0 && !x0) return MPM_ERR_INVALID_ARG;
+    for (int64_t e = 0; e < 3 * n_ext; e++)
+        if (!std::isfinite(x0[e])) return MPM_ERR_INVALID_ARG;
+    // every particle must start inside the valid domain [dx, (res-2) dx)
+    {
+        int64_t e = 0;
+        for (int i = 0; i < n_inst; i++)
+            for (int64_t p = 0; p < counts[i]; p++, e++)
+                for (int k = 0; k < 3; k++) {
+                    const double X = x0[3 * e + k] / cfgs[i].dx;
+                    if (!(X >= 1.0 && X < cfgs[i].res[k] - 2)) return MPM_ERR_OUT_OF_DOMAIN;
+                }
+    }
+    if (opts && (opts->checkpoint_every < 1 || !(opts->clip_value > 0) || !(opts->sigma_min > 0) ||
+                 opts->sort_every < 0))
+        return MPM_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return MPM_ERR_NO_DEVICE;
+    }
+    mpm_handle* h = new (std::nothrow) mpm_handle();
+    if (!h) return MPM_ERR_OOM;
+    cudaGetDevice(&h->device);
+    h->opt.checkpoint_every = 50;
+    h->opt.clip_grads = 0;
+    h->opt.clip_value = 1e4;
+    h->opt.sigma_min = 1e-4;
+    h->opt.sort_every = 0;
+    if (opts) h->opt = *opts;
+    h->n_ext = n_ext;
+    long long pbeg = 0, node = 0;
+    int blk = 0, chunks = 0;
+    int64_t ext = 0;
+    h->inst.resize(n_inst);
+    for (int i = 0; i < n_inst; i++) {
+        Instance& I = h->inst[i];
+        I.cfg = cfgs[i];
+        I.mat = mats[i];
+        I.n = counts[i];
+        I.ext_off = ext;
+        ext += I.n;
+        I.pbeg = pbeg;
+        I.n_chunks = (int)((I.n + kChunk - 1) / kChunk);
+        pbeg += (long long)I.n_chunks * kChunk;
+        chunks += I.n_chunks;
+        for (int k = 0; k < 3; k++) I.nb[k] = (I.cfg.res[k] + 3) / 4;
+        I.n_blocks = I.nb[0] * I.nb[1] * I.nb[2];
+        I.blk_off = blk;
+        I.node_off = node;
+        blk += I.n_blocks;
+        node += (long long)I.n_blocks * 64;
+    }
+    h->ncap = std::max(pbeg, (long long)kChunk);
+    h->n_chunks = chunks;
+    h->n_blocks = blk;
+    h->n_nodes = node;
+    int rc = MPM_OK;
+    auto fail = [&](int r) {
+        mpm_destroy(h);
+        return r;
+    };
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return MPM_ERR_CUDA;
+    }
+    h->own_stream = true;
+    if ((rc = h->d_inst.ensure(n_inst, h->device_bytes)) || (rc = h->d_chunk_inst.ensure(std::max(chunks, 1), h->device_bytes)) ||
+        (rc = h->d_block_inst.ensure(blk, h->device_bytes)) || (rc = h->d_ext_of_slot.ensure(h->ncap, h->device_bytes)) ||
+        (rc = h->d_state.ensure((size_t)h->ncap * kStateComps, h->device_bytes)) ||
+        (rc = h->d_x0.ensure((size_t)std::max<int64_t>(n_ext, 1) * 3, h->device_bytes)) ||
+        (rc = h->d_acc.ensure(node, h->device_bytes)) || (rc = h->d_vout.ensure(node, h->device_bytes)) ||
+        (rc = h->d_flags.ensure(blk, h->device_bytes)) || (rc = h->d_status.ensure(1, h->device_bytes)) ||
+        (rc = h->d_fp64.ensure(1, h->device_bytes)) || (rc = h->d_loss.ensure(n_inst, h->device_bytes)))
+        return fail(rc);
+    std::vector<int> ci(std::max(chunks, 1), 0), bi(blk), eos(h->ncap, -1);
+    for (int i = 0; i < n_inst; i++) {
+        const Instance& I = h->inst[i];
+        for (int c = 0; c < I.n_chunks; c++) ci[(I.pbeg / kChunk) + c] = i;
+        for (int b = 0; b < I.n_blocks; b++) bi[I.blk_off + b] = i;
+        for (int64_t p = 0; p < I.n; p++) eos[I.pbeg + p] = (int)(I.ext_off + p);
+    }
+    cudaStream_t s = h->stream;
+    if (cudaMemcpyAsync(h->d_chunk_inst.p, ci.data(), ci.size() * sizeof(int), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(h->d_block_inst.p, bi.data(), bi.size() * sizeof(int), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(h->d_ext_of_slot.p, eos.data(), eos.size() * sizeof(int), cudaMemcpyHostToDevice, s) ||
+        (n_ext > 0 && cudaMemcpyAsync(h->d_x0.p, x0, (size_t)n_ext * 3 * sizeof(float), cudaMemcpyHostToDevice, s)) ||
+        cudaMemsetAsync(h->d_acc.p, 0, node * sizeof(float4), s) ||
+        cudaMemsetAsync(h->d_vout.p, 0, node * sizeof(float4), s) || cudaMemsetAsync(h->d_flags.p, 0, blk, s) ||
+        cudaMemsetAsync(h->d_status.p, 0, sizeof(int), s) ||
+        cudaMemsetAsync(h->d_fp64.p, 0, sizeof(unsigned long long), s) ||
+        cudaStreamSynchronize(s)) {
+        cudaGetLastError();
+        return fail(MPM_ERR_CUDA);
+    }
+    if ((rc = upload_poses(h))) return fail(rc);
+    if ((rc = mpm_reset(h))) return fail(rc);
+    *out = h;
+    return MPM_OK;
+}
+
+void mpm_destroy(mpm_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->d_inst.release(); h->d_chunk_inst.release(); h->d_block_inst.release(); h->d_ext_of_slot.release();
+    h->d_state.release(); h->d_x0.release(); h->d_stage.release(); h->d_poses.release(); h->d_target.release();
+    h->d_acc.release(); h->d_vout.release(); h->d_flags.release(); h->d_status.release(); h->d_fp64.release();
+    h->d_loss.release();
+    for (auto& c : h->ckpt) c.release();
+    h->d_seg_state.release(); h->d_seg_acc.release(); h->d_seg_vout.release(); h->d_gacc.release();
+    h->d_seg_flags.release(); h->d_adj.release(); h->d_gmat.release(); h->d_gpose.release();
+    h->prof.release();
+    if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int mpm_set_stream(mpm_handle* h, void* stream) {
+    if (!h) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    CK(cudaStreamSynchronize(h->stream));
+    // all later work is issued on the caller's stream (ordered with the
+    // caller's own work); the library's private stream is released
+    if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
+    h->stream = (cudaStream_t)stream;
+    h->own_stream = false;
+    return MPM_OK;
+}
+
+int mpm_synchronize(mpm_handle* h) {
+    if (!h) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPM_OK;
+}
+
+int mpm_set_material(mpm_handle* h, int inst, const mpm_material* mat) {
+    RK(check_inst(h, inst));
+    if (!mat) return MPM_ERR_INVALID_ARG;
+    RK(validate_material(*mat));
+    RK(set_device(h));
+    h->inst[inst].mat = *mat;
+    h->recording = false;
+    return upload_instances(h);
+}
+
+int mpm_set_shovel_actions(mpm_handle* h, int inst, const double start_pose[4], int n_actions, const double* actions,
+                           int substeps_per_action) {
+    RK(check_inst(h, inst));
+    if (!start_pose || n_actions < 0 || (n_actions > 0 && !actions) || substeps_per_action < 1)
+        return MPM_ERR_INVALID_ARG;
+    if ((long long)n_actions * substeps_per_action > 100000000LL) return MPM_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; k++)
+        if (!std::isfinite(start_pose[k])) return MPM_ERR_INVALID_ARG;
+    for (long long t = 0; t < n_actions; t++) {
+        for (int k = 0; k < 6; k++)
+            if (!std::isfinite(actions[t * 6 + k])) return MPM_ERR_INVALID_ARG;
+        if (actions[t * 6 + 4] != 0.0 || actions[t * 6 + 5] != 0.0) return MPM_ERR_INVALID_ARG;
+    }
+    RK(set_device(h));
+    Instance& I = h->inst[inst];
+    I.has_traj = true;
+    I.has_skill = false;
+    std::memcpy(I.start, start_pose, sizeof I.start);
+    I.spa = substeps_per_action;
+    I.actions.assign(actions, actions + (size_t)n_actions * 6);
+    I.jac.clear();
+    h->recording = false;
+    return upload_poses(h);
+}
+
+int mpm_set_shovel_trajectory(mpm_handle* h, int inst, const mpm_skill* skill) {
+    RK(check_inst(h, inst));
+    if (!skill || skill->substeps_per_action < 1 || !finite_pos(skill->v_lin) || !finite_pos(skill->v_ang))
+        return MPM_ERR_INVALID_ARG;
+    for (int k = 0; k < 6; k++)
+        if (!std::isfinite(skill->theta[k]) || std::fabs(skill->theta[k]) > 1.0 + 1e-12) return MPM_ERR_INVALID_ARG;
+    std::vector<double> act, jac;
+    const double dt_step = skill->substeps_per_action * h->inst[inst].cfg.dt;
+    RK(skill_to_actions(*skill, dt_step, act, jac));
+    RK(mpm_set_shovel_actions(h, inst, skill->start_pose, (int)(act.size() / 6), act.data(),
+                              skill->substeps_per_action));
+    Instance& I = h->inst[inst];
+    I.has_skill = true;
+    I.skill = *skill;
+    I.jac.swap(jac);
+    return MPM_OK;
+}
+
+int mpm_num_actions(mpm_handle* h, int inst) {
+    RK(check_inst(h, inst));
+    return (int)(h->inst[inst].actions.size() / 6);
+}
+
+int mpm_reset(mpm_handle* h) {
+    if (!h) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    CK(launch_state_from_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, h->d_x0.p, nullptr, nullptr, nullptr, h->d_state.p,
+                             h->stream));
+    h->launches++;
+    CK(cudaStreamSynchronize(h->stream));
+    h->substep = 0;
+    h->recording = false;
+    h->rec_len = 0;
+    return MPM_OK;
+}
+
+int mpm_set_state(mpm_handle* h, const float* x, const float* v, const float* C, const float* F, int device_ptrs) {
+    if (!h || !x) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    const float *dx = x, *dv = v, *dC = C, *dF = F;
+    if (!device_ptrs) {
+        RK(ensure_stage(h));
+        float* st = h->d_stage.p;
+        const size_t n = (size_t)h->n_ext;
+        CK(cudaMemcpyAsync(st, x, n * 3 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        dx = st;
+        if (v) { CK(cudaMemcpyAsync(st + 3 * n, v, n * 3 * sizeof(float), cudaMemcpyHostToDevice, h->stream)); dv = st + 3 * n; }
+        if (C) { CK(cudaMemcpyAsync(st + 6 * n, C, n * 9 * sizeof(float), cudaMemcpyHostToDevice, h->stream)); dC = st + 6 * n; }
+        if (F) { CK(cudaMemcpyAsync(st + 15 * n, F, n * 9 * sizeof(float), cudaMemcpyHostToDevice, h->stream)); dF = st + 15 * n; }
+    }
+    CK(launch_state_from_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, dx, dv, dC, dF, h->d_state.p, h->stream));
+    h->launches++;
+    h->recording = false;
+    h->rec_len = 0;
+    if (!device_ptrs) CK(cudaStreamSynchronize(h->stream));
+    return MPM_OK;
+}
+
+int mpm_get_state(mpm_handle* h, float* x, float* v, float* C, float* F, int device_ptrs) {
+    if (!h) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    if (device_ptrs) {
+        CK(launch_state_to_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, h->d_state.p, x, v, C, F, h->stream));
+        h->launches++;
+        return MPM_OK;
+    }
+    RK(ensure_stage(h));
+    float* st = h->d_stage.p;
+    const size_t n = (size_t)h->n_ext;
+    CK(launch_state_to_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, h->d_state.p, st, st + 3 * n, st + 6 * n, st + 15 * n,
+                           h->stream));
+    h->launches++;
+    if (x) CK(cudaMemcpyAsync(x, st, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (v) CK(cudaMemcpyAsync(v, st + 3 * n, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (C) CK(cudaMemcpyAsync(C, st + 6 * n, n * 9 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (F) CK(cudaMemcpyAsync(F, st + 15 * n, n * 9 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPM_OK;
+}
+
+int mpm_forward(mpm_handle* h, int n_substeps, int record) {
+    if (!h || n_substeps < 0) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    const int K = h->opt.checkpoint_every;
+    if (record) {
+        if (!h->recording) {
+            h->recording = true;
+            h->rec_start = h->substep;
+            h->rec_len = 0;
+        }
+    } else {
+        h->recording = false;
+        h->rec_len = 0;
+    }
+    const size_t state_floats = (size_t)h->ncap * kStateComps;
+    StepArgs a = base_args(h);
+    a.sin = a.sout = h->d_state.p;
+    a.acc = h->d_acc.p;
+    a.vout = h->d_vout.p;
+    a.flags = h->d_flags.p;
+    a.keep_grid = 0;
+    for (int i = 0; i < n_substeps; i++) {
+        if (record && h->rec_len % K == 0) {
+            const size_t c = (size_t)(h->rec_len / K);
+            if (h->ckpt.size() <= c) h->ckpt.resize(c + 1);
+            RK(h->ckpt[c].ensure(state_floats, h->device_bytes));
+            CK(cudaMemcpyAsync(h->ckpt[c].p, h->d_state.p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice,
+                               h->stream));
+        }
+        a.substep = (int)h->substep;
+        RK(run_substep(h, a));
+        h->substep++;
+        if (record) h->rec_len++;
+    }
+    const int st = read_status(h);
+    if (st != MPM_OK) h->recording = false;
+    return st;
+}
+
+int mpm_loss_mse(mpm_handle* h, const float* x_target, double* loss, float* dL_dx, int device_ptrs) {
+    if (!h || !x_target || !loss) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    const size_t n = (size_t)h->n_ext;
+    const float* tgt = x_target;
+    float* out = dL_dx;
+    if (!device_ptrs) {
+        RK(h->d_target.ensure(std::max<size_t>(n, 1) * 6, h->device_bytes));
+        CK(cudaMemcpyAsync(h->d_target.p, x_target, n * 3 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        tgt = h->d_target.p;
+        out = dL_dx ? h->d_target.p + 3 * n : nullptr;
+    }
+    CK(cudaMemsetAsync(h->d_loss.p, 0, h->inst.size() * sizeof(double), h->stream));
+    CK(launch_loss_mse(h->d_inst.p, h->d_chunk_inst.p, h->n_chunks, h->ncap, h->d_ext_of_slot.p, h->d_state.p, tgt, out,
+                       h->d_loss.p, h->stream));
+    h->launches++;
+    CK(cudaMemcpyAsync(loss, h->d_loss.p, h->inst.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (!device_ptrs && dL_dx)
+        CK(cudaMemcpyAsync(dL_dx, out, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPM_OK;
+}
+
+int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, int device_ptrs, double* dL_dmaterial,
+                 double* dL_dtheta) {
+    if (!h) return MPM_ERR_INVALID_ARG;
+    if (!h->recording || h->rec_len == 0) return MPM_ERR_NO_RECORD;
+    RK(set_device(h));
+    const int K = h->opt.checkpoint_every;
+    const int n_inst = (int)h->inst.size();
+    const size_t state_floats = (size_t)h->ncap * kStateComps;
+    const int seg_cap = (int)std::min<int64_t>(K, h->rec_len);
+    RK(h->d_seg_state.ensure(state_floats * (seg_cap + 1), h->device_bytes));
+    const bool fresh_grids = h->d_seg_acc.n < (size_t)h->n_nodes * seg_cap;
+    RK(h->d_seg_acc.ensure((size_t)h->n_nodes * seg_cap, h->device_bytes));
+    RK(h->d_seg_vout.ensure((size_t)h->n_nodes * seg_cap, h->device_bytes));
+    RK(h->d_seg_flags.ensure((size_t)h->n_blocks * seg_cap, h->device_bytes));
+    const bool fresh_gacc = h->d_gacc.n < (size_t)h->n_nodes;
+    RK(h->d_gacc.ensure((size_t)h->n_nodes, h->device_bytes));
+    RK(h->d_adj.ensure(state_floats, h->device_bytes));
+    RK(h->d_gmat.ensure((size_t)n_inst * 4, h->device_bytes));
+    RK(h->d_gpose.ensure((size_t)h->rec_len * n_inst * 8, h->device_bytes));
+    cudaStream_t s = h->stream;
+    if (fresh_grids || !h->seg_grids_clean) {
+        CK(cudaMemsetAsync(h->d_seg_acc.p, 0, h->d_seg_acc.n * sizeof(float4), s));
+        CK(cudaMemsetAsync(h->d_seg_flags.p, 0, h->d_seg_flags.n, s));
+    }
+    if (fresh_gacc || !h->seg_grids_clean) CK(cudaMemsetAsync(h->d_gacc.p, 0, h->d_gacc.n * sizeof(float4), s));
+    h->seg_grids_clean = false;   // set again once every slot has been cleared
+    // seed the adjoint of the final state
+    const float *gx = dL_dx, *gv = dL_dv;
+    if (!device_ptrs && (dL_dx || dL_dv)) {
+        RK(ensure_stage(h));
+        const size_t n = (size_t)h->n_ext;
+        if (dL_dx) { CK(cudaMemcpyAsync(h->d_stage.p, dL_dx, n * 3 * sizeof(float), cudaMemcpyHostToDevice, s)); gx = h->d_stage.p; }
+        if (dL_dv) { CK(cudaMemcpyAsync(h->d_stage.p + 3 * n, dL_dv, n * 3 * sizeof(float), cudaMemcpyHostToDevice, s)); gv = h->d_stage.p + 3 * n; }
+    }
+    CK(launch_adj_from_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, gx, gv, h->d_adj.p, s));
+    h->launches++;
+    CK(cudaMemsetAsync(h->d_gmat.p, 0, (size_t)n_inst * 4 * sizeof(double), s));
+    CK(cudaMemsetAsync(h->d_gpose.p, 0, (size_t)h->rec_len * n_inst * 8 * sizeof(double), s));
+
+    const int64_t n_seg = (h->rec_len + K - 1) / K;
+    for (int64_t j = n_seg - 1; j >= 0; j--) {
+        const int64_t seg_begin = j * K;
+        const int seg_len = (int)std::min<int64_t>(K, h->rec_len - seg_begin);
+        CK(cudaMemcpyAsync(h->d_seg_state.p, h->ckpt[j].p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        // recompute the segment, keeping every state and grid
+        for (int i = 0; i < seg_len; i++) {
+            StepArgs a = base_args(h);
+            a.sin = h->d_seg_state.p + state_floats * i;
+            a.sout = h->d_seg_state.p + state_floats * (i + 1);
+            a.acc = h->d_seg_acc.p + (size_t)h->n_nodes * i;
+            a.vout = h->d_seg_vout.p + (size_t)h->n_nodes * i;
+            a.flags = h->d_seg_flags.p + (size_t)h->n_blocks * i;
+            a.keep_grid = 1;
+            a.substep = (int)(h->rec_start + seg_begin + i);
+            RK(run_substep(h, a));
+        }
+        // reverse it
+        for (int i = seg_len - 1; i >= 0; i--) {
+            AdjArgs A;
+            std::memset(&A, 0, sizeof A);
+            A.f = base_args(h);
+            A.f.sin = A.f.sout = h->d_seg_state.p + state_floats * i;
+            A.f.acc = h->d_seg_acc.p + (size_t)h->n_nodes * i;
+            A.f.vout = h->d_seg_vout.p + (size_t)h->n_nodes * i;
+            A.f.flags = h->d_seg_flags.p + (size_t)h->n_blocks * i;
+            A.f.keep_grid = 1;
+            A.f.substep = (int)(h->rec_start + seg_begin + i);
+            A.adj = h->d_adj.p;
+            A.gacc = h->d_gacc.p;
+            A.gmat = h->d_gmat.p;
+            A.gpose = h->d_gpose.p + (size_t)(seg_begin + i) * n_inst * 8;
+            RK(run_adjoint_substep(h, A));
+        }
+    }
+    h->seg_grids_clean = true;
+    std::vector<double> gm((size_t)n_inst * 4), gp((size_t)h->rec_len * n_inst * 8);
+    CK(cudaMemcpyAsync(gm.data(), h->d_gmat.p, gm.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(gp.data(), h->d_gpose.p, gp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int st = read_status(h);
+    // material chain: mu(E, nu), lambda(E, nu), alpha(phi), m_p = rho V_p
+    for (int i = 0; i < n_inst; i++) {
+        const Instance& I = h->inst[i];
+        const double E = I.mat.E, nu = I.mat.nu;
+        const double gmu = gm[4 * i], glam = gm[4 * i + 1], galpha = gm[4 * i + 2], gmp = gm[4 * i + 3];
+        const double dmu_dE = 1.0 / (2.0 * (1.0 + nu)), dmu_dnu = -E / (2.0 * (1.0 + nu) * (1.0 + nu));
+        const double dl_dE = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+        const double dl_dnu = E * (1.0 + 2.0 * nu * nu) / ((1.0 + nu) * (1.0 + nu) * (1.0 - 2.0 * nu) * (1.0 - 2.0 * nu));
+        const double phi = I.mat.phi_deg * kPi / 180.0, sp = std::sin(phi);
+        const double da_dphi = std::sqrt(2.0 / 3.0) * 6.0 * std::cos(phi) / ((3.0 - sp) * (3.0 - sp));
+        if (dL_dmaterial) {
+            dL_dmaterial[4 * i + 0] = gmu * dmu_dE + glam * dl_dE;
+            dL_dmaterial[4 * i + 1] = gmu * dmu_dnu + glam * dl_dnu;
+            dL_dmaterial[4 * i + 2] = gmp * I.cfg.particle_volume;
+            dL_dmaterial[4 * i + 3] = galpha * da_dphi * kPi / 180.0;
+        }
+    }
+    // pose adjoints -> action adjoints -> skill parameters
+    for (int i = 0; i < n_inst; i++) {
+        Instance& I = h->inst[i];
+        const int na = (int)(I.actions.size() / 6);
+        I.gactions.assign((size_t)na * 6, 0.0);
+        for (int k = 0; k < 4; k++) I.gstart[k] = 0.0;
+        if (!I.has_traj || I.n_poses == 0) {
+            if (dL_dtheta)
+                for (int k = 0; k < 6; k++) dL_dtheta[6 * i + k] = 0.0;
+            continue;
+        }
+        // gradient per table entry; substeps past the table use its last pose
+        std::vector<double> tab((size_t)I.n_poses * 8, 0.0);
+        for (int64_t r = 0; r < h->rec_len; r++) {
+            const int64_t sidx = h->rec_start + r;
+            const double* g = &gp[((size_t)r * n_inst + i) * 8];
+            if (sidx < I.n_poses) {
+                for (int k = 0; k < 8; k++) tab[(size_t)sidx * 8 + k] += g[k];
+            } else {
+                for (int k = 0; k < 4; k++) tab[(size_t)(I.n_poses - 1) * 8 + k] += g[k];
+            }
+        }
+        double suffix[4] = {0, 0, 0, 0};
+        for (int64_t sidx = I.n_poses - 1; sidx >= 0; sidx--) {
+            for (int k = 0; k < 4; k++) suffix[k] += tab[(size_t)sidx * 8 + k];
+            const int64_t t = sidx / I.spa;
+            if (t >= na) continue;
+            for (int k = 0; k < 4; k++)
+                I.gactions[(size_t)t * 6 + k] += (suffix[k] + tab[(size_t)sidx * 8 + 4 + k] / I.cfg.dt) / I.spa;
+        }
+        for (int k = 0; k < 4; k++) I.gstart[k] = suffix[k];
+        if (dL_dtheta) {
+            for (int j = 0; j < 6; j++) {
+                double g = 0.0;
+                if (I.has_skill)
+                    for (int t = 0; t < na; t++)
+                        for (int k = 0; k < 6; k++) g += I.gactions[(size_t)t * 6 + k] * I.jac[(size_t)t * 36 + k * 6 + j];
+                dL_dtheta[6 * i + j] = g;
+            }
+        }
+    }
+    h->recording = false;
+    h->have_grad = true;
+    return st;
+}
+
+int mpm_get_state_grad(mpm_handle* h, float* gx, float* gv, float* gC, float* gF, int device_ptrs) {
+    if (!h) return MPM_ERR_INVALID_ARG;
+    if (!h->have_grad) return MPM_ERR_NO_RECORD;
+    RK(set_device(h));
+    if (device_ptrs) {
+        CK(launch_state_to_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, h->d_adj.p, gx, gv, gC, gF, h->stream));
+        h->launches++;
+        return MPM_OK;
+    }
+    RK(ensure_stage(h));
+    float* st = h->d_stage.p;
+    const size_t n = (size_t)h->n_ext;
+    CK(launch_state_to_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, h->d_adj.p, st, st + 3 * n, st + 6 * n, st + 15 * n,
+                           h->stream));
+    h->launches++;
+    if (gx) CK(cudaMemcpyAsync(gx, st, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (gv) CK(cudaMemcpyAsync(gv, st + 3 * n, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (gC) CK(cudaMemcpyAsync(gC, st + 6 * n, n * 9 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (gF) CK(cudaMemcpyAsync(gF, st + 15 * n, n * 9 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPM_OK;
+}
+
+int mpm_get_action_grad(mpm_handle* h, int inst, double* dL_dactions, double* dL_dstart) {
+    RK(check_inst(h, inst));
+    if (!h->have_grad) return MPM_ERR_NO_RECORD;
+    const Instance& I = h->inst[inst];
+    if (dL_dactions && !I.gactions.empty())
+        std::memcpy(dL_dactions, I.gactions.data(), I.gactions.size() * sizeof(double));
+    if (dL_dstart) std::memcpy(dL_dstart, I.gstart, sizeof I.gstart);
+    return MPM_OK;
+}
+
+int mpm_set_substep(mpm_handle* h, int64_t substep) {
+    if (!h || substep < 0 || substep > (1LL << 30)) return MPM_ERR_INVALID_ARG;
+    h->substep = substep;
+    h->recording = false;
+    h->rec_len = 0;
+    return MPM_OK;
+}
+
+int mpm_profile(mpm_handle* h, int enable) {
+    if (!h) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    h->prof.reset();
+    h->prof.on = enable != 0;
+    return MPM_OK;
+}
+
+int mpm_profile_read(mpm_handle* h, int kernel, double* total_ms, int64_t* launches) {
+    if (!h || kernel < 0 || kernel >= (int)KernelId::Count) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    h->prof.flush();
+    if (total_ms) *total_ms = h->prof.total_ms[kernel];
+    if (launches) *launches = h->prof.count[kernel];
+    return MPM_OK;
+}
+
+const char* mpm_kernel_name(int kernel) {
+    static const char* names[] = {"k_p2g", "k_grid", "k_g2p", "k_g2p_bwd", "k_grid_bwd", "k_p2g_bwd", "k_grid_clear"};
+    if (kernel < 0 || kernel >= (int)KernelId::Count) return "";
+    return names[kernel];
+}
+
+int mpm_grid_mass(mpm_handle* h, double* mass) {
+    if (!h || !mass) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    CK(cudaMemsetAsync(h->d_loss.p, 0, h->inst.size() * sizeof(double), h->stream));
+    CK(launch_grid_mass(h->d_inst.p, h->d_block_inst.p, h->n_blocks, h->d_vout.p, h->d_loss.p, h->stream));
+    h->launches++;
+    CK(cudaMemcpyAsync(mass, h->d_loss.p, h->inst.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPM_OK;
+}
+
+int mpm_get_info(mpm_handle* h, mpm_info_t* out) {
+    if (!h || !out) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    unsigned long long fb = 0;
+    CK(cudaMemcpyAsync(&fb, h->d_fp64.p, sizeof fb, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out->n_inst = (int)h->inst.size();
+    out->n_particles = h->n_ext;
+    out->substep = h->substep;
+    out->recorded = h->recording ? h->rec_len : 0;
+    out->device_bytes = h->device_bytes;
+    out->kernel_launches = h->launches;
+    out->fp64_fallbacks = (int64_t)fb;
+    return MPM_OK;
+}
+
+}  // extern "C"

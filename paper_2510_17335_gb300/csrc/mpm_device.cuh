@@ -1,0 +1,674 @@
+// Device-side physics of the MLS-MPM sand substep (DDBot, arXiv 2510.17335,
+// Sec. III-A, Algorithm 1, Eqs. (3)-(7)) and of its adjoint (Sec. III-D,
+// Appendix B), for sm_103a. FP32 state; the SVD + return mapping is redone in
+// FP64 for the rare ill-conditioned deformation gradient.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mpm_types.h"
+
+namespace mpm {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T dsqrt(T x);
+template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+template <typename T> __device__ __forceinline__ T dlog(T x);
+template <> __device__ __forceinline__ float dlog<float>(float x) { return logf(x); }
+template <> __device__ __forceinline__ double dlog<double>(double x) { return log(x); }
+template <typename T> __device__ __forceinline__ T dexp(T x);
+template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
+template <typename T> __device__ __forceinline__ T dexpm1(T x);
+template <> __device__ __forceinline__ float dexpm1<float>(float x) { return expm1f(x); }
+template <> __device__ __forceinline__ double dexpm1<double>(double x) { return expm1(x); }
+
+// Jacobi rotation threshold: skip when gpq^2 <= tol * gpp * gqq.
+template <typename T> __device__ __forceinline__ T jacobi_tol();
+template <> __device__ __forceinline__ float jacobi_tol<float>() { return 1e-14f; }
+template <> __device__ __forceinline__ double jacobi_tol<double>() { return 1e-30; }
+template <typename T> struct Sweeps;
+template <> struct Sweeps<float> { static constexpr int n = 4; };
+template <> struct Sweeps<double> { static constexpr int n = 10; };
+
+// ---------------------------------------------------------------------------
+// 3x3 SVD: cyclic Jacobi eigen-decomposition of G = F^T F (gives V and
+// sigma^2), then U from the columns of F V. U and V are proper rotations; the
+// smallest singular value carries the sign of det F.
+// ---------------------------------------------------------------------------
+template <typename T, int p, int q, int r>
+__device__ __forceinline__ void jacobi_rotate(T (&G)[3][3], T (&V)[3][3]) {
+    const T gpq = G[p][q], gpp = G[p][p], gqq = G[q][q];
+    if (gpq * gpq <= jacobi_tol<T>() * gpp * gqq) return;
+    const T zeta = (gqq - gpp) / (T(2) * gpq);
+    T t;
+    if (fabs(zeta) > T(1e15))
+        t = T(0.5) / zeta;
+    else
+        t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + dsqrt<T>(T(1) + zeta * zeta));
+    const T c = T(1) / dsqrt<T>(T(1) + t * t), s = c * t;
+    G[p][p] = gpp - t * gpq;
+    G[q][q] = gqq + t * gpq;
+    G[p][q] = G[q][p] = T(0);
+    const T grp = G[r][p], grq = G[r][q];
+    G[r][p] = G[p][r] = c * grp - s * grq;
+    G[r][q] = G[q][r] = s * grp + c * grq;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const T a = V[k][p], b = V[k][q];
+        V[k][p] = c * a - s * b;
+        V[k][q] = s * a + c * b;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3], T (&V)[3][3]) {
+    T G[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            G[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+            V[i][j] = (i == j) ? T(1) : T(0);
+        }
+#pragma unroll
+    for (int sw = 0; sw < Sweeps<T>::n; sw++) {
+        jacobi_rotate<T, 0, 1, 2>(G, V);
+        jacobi_rotate<T, 0, 2, 1>(G, V);
+        jacobi_rotate<T, 1, 2, 0>(G, V);
+    }
+    // order: i = largest, m = smallest, j = the middle one
+    const T l0 = G[0][0], l1 = G[1][1], l2 = G[2][2];
+    int m = 0;
+    if (l1 < l0) m = 1;
+    if (l2 < (m == 0 ? l0 : l1)) m = 2;
+    int i = (m == 0) ? 1 : 0;
+    int j = 3 - m - i;
+    const T li = (i == 0) ? l0 : l1;
+    const T lj = (j == 1) ? l1 : l2;
+    if (lj > li) { int tmp = i; i = j; j = tmp; }
+    // B = F V, column k
+    T b[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) b[r][k] = F[r][0] * V[0][k] + F[r][1] * V[1][k] + F[r][2] * V[2][k];
+    T bi[3], bj[3], bm[3];
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        bi[r] = (i == 0) ? b[r][0] : ((i == 1) ? b[r][1] : b[r][2]);
+        bj[r] = (j == 0) ? b[r][0] : ((j == 1) ? b[r][1] : b[r][2]);
+        bm[r] = (m == 0) ? b[r][0] : ((m == 1) ? b[r][1] : b[r][2]);
+    }
+    T ui[3], uj[3], um[3];
+    T si = dsqrt<T>(bi[0] * bi[0] + bi[1] * bi[1] + bi[2] * bi[2]);
+    if (!(si > T(1e-30))) {
+        // F == 0: any rotations will do
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) U[r][k] = (r == k) ? T(1) : T(0);
+        s[0] = s[1] = s[2] = T(0);
+        return;
+    }
+    const T inv_si = T(1) / si;
+#pragma unroll
+    for (int r = 0; r < 3; r++) ui[r] = bi[r] * inv_si;
+    const T dij = ui[0] * bj[0] + ui[1] * bj[1] + ui[2] * bj[2];
+#pragma unroll
+    for (int r = 0; r < 3; r++) uj[r] = bj[r] - dij * ui[r];
+    T sj = dsqrt<T>(uj[0] * uj[0] + uj[1] * uj[1] + uj[2] * uj[2]);
+    if (!(sj > T(1e-30) * si)) {
+        // rank one: any unit vector orthogonal to u_i
+        int a = 0;
+        if (fabs(ui[1]) < fabs(ui[a])) a = 1;
+        if (fabs(ui[2]) < fabs(ui[a])) a = 2;
+        T e[3] = {T(0), T(0), T(0)};
+        e[a] = T(1);
+        const T d = ui[a];
+#pragma unroll
+        for (int r = 0; r < 3; r++) uj[r] = e[r] - d * ui[r];
+        const T ne = dsqrt<T>(uj[0] * uj[0] + uj[1] * uj[1] + uj[2] * uj[2]);
+#pragma unroll
+        for (int r = 0; r < 3; r++) uj[r] /= ne;
+        sj = uj[0] * bj[0] + uj[1] * bj[1] + uj[2] * bj[2];
+    } else {
+        const T inv = T(1) / sj;
+#pragma unroll
+        for (int r = 0; r < 3; r++) uj[r] *= inv;
+        sj = uj[0] * bj[0] + uj[1] * bj[1] + uj[2] * bj[2];
+    }
+    // u_m completes a right-handed frame: (i, j, m) cyclic -> u_i x u_j
+    const T par = (((j - i + 3) % 3) == 1) ? T(1) : T(-1);
+    um[0] = par * (ui[1] * uj[2] - ui[2] * uj[1]);
+    um[1] = par * (ui[2] * uj[0] - ui[0] * uj[2]);
+    um[2] = par * (ui[0] * uj[1] - ui[1] * uj[0]);
+    const T sm = um[0] * bm[0] + um[1] * bm[1] + um[2] * bm[2];
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        const T c0 = (i == 0) ? ui[r] : ((j == 0) ? uj[r] : um[r]);
+        const T c1 = (i == 1) ? ui[r] : ((j == 1) ? uj[r] : um[r]);
+        const T c2 = (i == 2) ? ui[r] : ((j == 2) ? uj[r] : um[r]);
+        U[r][0] = c0;
+        U[r][1] = c1;
+        U[r][2] = c2;
+    }
+    s[i] = si;
+    s[j] = sj;
+    s[m] = sm;
+}
+
+// ---------------------------------------------------------------------------
+// Drucker-Prager return on the singular values and the SVK log-strain
+// stress eigenvalues (Eqs. (3)-(7)).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Spectral {
+    T U[3][3], V[3][3], s[3];
+    T eps[3], deps[3];    // ln max(s, s_min) and its derivative in s
+    T ehat[3], nh, tr, kappa;
+    T shat[3], e[3], t[3];
+    int kase;             // 0: tr > 0 (apex, S^ = I); 1: inside the cone; 2: onto the cone
+};
+
+template <typename T>
+__device__ __forceinline__ void return_map(Spectral<T>& S, T mu, T lam, T beta, T smin) {
+    S.tr = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const bool ok = S.s[k] > smin;
+        S.eps[k] = dlog<T>(ok ? S.s[k] : smin);
+        S.deps[k] = ok ? T(1) / S.s[k] : T(0);
+        S.tr += S.eps[k];
+    }
+    T n2 = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        S.ehat[k] = S.eps[k] - S.tr * T(1.0 / 3.0);
+        n2 += S.ehat[k] * S.ehat[k];
+    }
+    S.nh = dsqrt<T>(n2);
+    const T dg = S.nh + beta * S.tr;
+    S.kappa = T(0);
+    if (S.tr > T(0)) {
+        S.kase = 0;
+#pragma unroll
+        for (int k = 0; k < 3; k++) { S.shat[k] = T(1); S.e[k] = T(0); }
+    } else if (dg <= T(0) || S.nh <= T(1e-12)) {
+        S.kase = 1;
+#pragma unroll
+        for (int k = 0; k < 3; k++) { S.shat[k] = S.s[k]; S.e[k] = S.eps[k]; }
+    } else {
+        S.kase = 2;
+        const T r = dg / S.nh;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            S.e[k] = S.eps[k] - r * S.ehat[k];
+            S.shat[k] = dexp<T>(S.e[k]);
+        }
+        S.kappa = -beta * S.tr / S.nh;
+    }
+    const T se = S.e[0] + S.e[1] + S.e[2];
+#pragma unroll
+    for (int k = 0; k < 3; k++) S.t[k] = T(2) * mu * S.e[k] + lam * se;
+}
+
+// trial F -> spectral data (SVD + return mapping)
+template <typename T>
+__device__ __forceinline__ void constitutive_spectral(const T (&Ft)[3][3], T mu, T lam, T beta, T smin,
+                                                      Spectral<T>& S) {
+    svd3<T>(Ft, S.U, S.s, S.V);
+    return_map<T>(S, mu, lam, beta, smin);
+}
+
+// F' = U diag(shat) V^T and tau = U diag(t) U^T
+template <typename T, typename O>
+__device__ __forceinline__ void spectral_outputs(const Spectral<T>& S, O (&Fn)[3][3], O (&tau)[3][3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            T f = T(0), g = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                f += S.U[a][k] * S.shat[k] * S.V[b][k];
+                g += S.U[a][k] * S.t[k] * S.U[b][k];
+            }
+            Fn[a][b] = O(f);
+            tau[a][b] = O(g);
+        }
+}
+
+// ill-conditioned or non-finite FP32 results are redone in FP64
+__device__ __forceinline__ bool needs_fp64(const Spectral<float>& S) {
+    const float amax = fmaxf(fabsf(S.s[0]), fmaxf(fabsf(S.s[1]), fabsf(S.s[2])));
+    const float amin = fminf(fabsf(S.s[0]), fminf(fabsf(S.s[1]), fabsf(S.s[2])));
+    return !(amin >= 1e-3f * amax) || !isfinite(amax);
+}
+
+// forward constitutive step with the FP64 fallback kept out of line
+__device__ __noinline__ void constitutive_fp64(const float (&Ft)[3][3], float mu, float lam, float beta, float smin,
+                                               float (&Fn)[3][3], float (&tau)[3][3]) {
+    double Fd[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) Fd[a][b] = Ft[a][b];
+    Spectral<double> S;
+    constitutive_spectral<double>(Fd, mu, lam, beta, smin, S);
+    spectral_outputs<double, float>(S, Fn, tau);
+}
+
+__device__ __forceinline__ bool constitutive(const float (&Ft)[3][3], float mu, float lam, float beta, float smin,
+                                             float (&Fn)[3][3], float (&tau)[3][3]) {
+    Spectral<float> S;
+    constitutive_spectral<float>(Ft, mu, lam, beta, smin, S);
+    if (needs_fp64(S)) {
+        constitutive_fp64(Ft, mu, lam, beta, smin, Fn, tau);
+        return true;
+    }
+    spectral_outputs<float, float>(S, Fn, tau);
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the constitutive step. In the frame K = U^T dFt V the diagonal
+// carries d(sigma); each pair (i, j) of the off-diagonal mixes through the
+// divided differences (f_i - f_j)/(s_i - s_j) and (f_i + f_j)/(s_i + s_j) of
+// the isotropic maps s -> shat and s -> t. The first quotient is evaluated
+// through expm1 so that it stays exact at s_i = s_j.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T xm1(T x) { return x == T(0) ? T(1) : x / dexpm1<T>(x); }
+template <typename T>
+__device__ __forceinline__ T em1ratio(T k, T x) { return x == T(0) ? k : dexpm1<T>(k * x) / dexpm1<T>(x); }
+
+template <typename T>
+__device__ __forceinline__ void constitutive_adjoint_spectral(const Spectral<T>& S, T mu, T lam, T alpha, T beta,
+                                                              T smin, const T (&gFn)[3][3], const T (&gtau)[3][3],
+                                                              T (&gFt)[3][3], T& gmu, T& glam, T& galpha) {
+    // rotate the output adjoints into the singular frames
+    T G[3][3], Tt[3][3], tmp[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            T x = T(0), y = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                x += S.U[k][a] * gFn[k][b];
+                y += S.U[k][a] * gtau[k][b];
+            }
+            tmp[a][b] = x;
+            Tt[a][b] = y;   // U^T gtau (right factor below)
+        }
+    T Th[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            T x = T(0), y = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                x += tmp[a][k] * S.V[k][b];
+                y += Tt[a][k] * S.U[k][b];
+            }
+            G[a][b] = x;
+            Th[a][b] = y;
+        }
+    // Jacobians in sigma: Je = de/ds, Jsh = dshat/ds; and d/dbeta
+    T Je[3][3], Jsh[3][3], de_db[3], dsh_db[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        de_db[a] = T(0);
+        dsh_db[a] = T(0);
+#pragma unroll
+        for (int b = 0; b < 3; b++) { Je[a][b] = T(0); Jsh[a][b] = T(0); }
+    }
+    if (S.kase == 1) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) { Je[a][a] = S.deps[a]; Jsh[a][a] = T(1); }
+    } else if (S.kase == 2) {
+        const T inv_nh = T(1) / S.nh;
+        T eh[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) eh[a] = S.ehat[a] * inv_nh;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                const T P = (a == b ? T(1) : T(0)) - T(1.0 / 3.0);
+                const T d = T(1.0 / 3.0) - beta * (eh[a] + S.tr * (P - eh[a] * eh[b]) * inv_nh);
+                Je[a][b] = d * S.deps[b];
+                Jsh[a][b] = S.shat[a] * Je[a][b];
+            }
+            de_db[a] = -S.tr * eh[a];
+            dsh_db[a] = S.shat[a] * de_db[a];
+        }
+    }
+    // t = 2 mu e + lam (sum e)
+    T Jt[3][3], dt_db[3];
+    const T sdb = de_db[0] + de_db[1] + de_db[2];
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const T cs = Je[0][b] + Je[1][b] + Je[2][b];
+#pragma unroll
+        for (int a = 0; a < 3; a++) Jt[a][b] = T(2) * mu * Je[a][b] + lam * cs;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) dt_db[a] = T(2) * mu * de_db[a] + lam * sdb;
+    T K[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        T g = T(0);
+#pragma unroll
+        for (int a = 0; a < 3; a++) g += G[a][a] * Jsh[a][b] + Th[a][a] * Jt[a][b];
+#pragma unroll
+        for (int a = 0; a < 3; a++) K[a][b] = (a == b) ? g : T(0);
+    }
+    T gb = T(0);
+    const T se = S.e[0] + S.e[1] + S.e[2];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        gb += G[a][a] * dsh_db[a] + Th[a][a] * dt_db[a];
+        gmu += Th[a][a] * T(2) * S.e[a];
+        glam += Th[a][a] * se;
+    }
+    if (S.kase == 2) {
+        const T c = T(1) + T(1.5) * lam / mu;
+        gmu += gb * alpha * (T(-1.5) * lam / (mu * mu));
+        glam += gb * alpha * (T(1.5) / mu);
+        galpha += gb * c;
+    }
+    // off-diagonal pairs
+#pragma unroll
+    for (int pr = 0; pr < 3; pr++) {
+        const int i = (pr == 2) ? 1 : 0;
+        const int j = (pr == 0) ? 1 : 2;
+        const T si = S.s[i], sj = S.s[j];
+        const bool smooth = (si > smin) && (sj > smin);
+        const T dsig = si - sj;
+        T sum = si + sj;
+        if (fabs(sum) < T(1e-30)) sum = T(1e-30);
+        const bool close = fabs(dsig) <= T(1e-6) * fmax(fabs(si), fabs(sj));
+        T ds, dd, q1;
+        if (S.kase == 0) {
+            ds = T(0);
+            dd = T(2) / sum;
+            q1 = T(0);
+        } else if (S.kase == 1) {
+            ds = T(1);
+            dd = T(1);
+            if (smooth)
+                q1 = T(2) * mu * xm1<T>(S.eps[i] - S.eps[j]) / sj;
+            else
+                q1 = close ? (Jt[i][i] - Jt[i][j]) : (S.t[i] - S.t[j]) / dsig;
+        } else {
+            if (smooth) {
+                const T D = S.eps[i] - S.eps[j];
+                ds = S.shat[j] / sj * em1ratio<T>(S.kappa, D);
+                q1 = T(2) * mu * S.kappa * xm1<T>(D) / sj;
+            } else {
+                ds = close ? (Jsh[i][i] - Jsh[i][j]) : (S.shat[i] - S.shat[j]) / dsig;
+                q1 = close ? (Jt[i][i] - Jt[i][j]) : (S.t[i] - S.t[j]) / dsig;
+            }
+            dd = (S.shat[i] + S.shat[j]) / sum;
+        }
+        const T q2 = (S.t[i] - S.t[j]) / sum;
+        const T a = T(0.5) * (ds + dd), b = T(0.5) * (ds - dd);
+        const T Gij = G[i][j], Gji = G[j][i];
+        const T St = Th[i][j] + Th[j][i];
+        K[i][j] = a * Gij + b * Gji + T(0.5) * St * (q1 - q2);
+        K[j][i] = b * Gij + a * Gji + T(0.5) * St * (q1 + q2);
+    }
+    // gFt = U K V^T
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            T x = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) x += S.U[a][k] * K[k][b];
+            tmp[a][b] = x;
+        }
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            T x = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) x += tmp[a][k] * S.V[b][k];
+            gFt[a][b] = x;
+        }
+}
+
+__device__ __noinline__ void constitutive_adjoint_fp64(const float (&Ft)[3][3], float mu, float lam, float alpha,
+                                                       float beta, float smin, const float (&gFn)[3][3],
+                                                       const float (&gtau)[3][3], float (&tau)[3][3],
+                                                       float (&gFt)[3][3], float& gmu, float& glam, float& galpha) {
+    double Fd[3][3], gF[3][3], gT[3][3], out[3][3], Fn[3][3], td[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) { Fd[a][b] = Ft[a][b]; gF[a][b] = gFn[a][b]; gT[a][b] = gtau[a][b]; }
+    Spectral<double> S;
+    constitutive_spectral<double>(Fd, mu, lam, beta, smin, S);
+    spectral_outputs<double, double>(S, Fn, td);
+    double m = 0, l = 0, al = 0;
+    constitutive_adjoint_spectral<double>(S, mu, lam, alpha, beta, smin, gF, gT, out, m, l, al);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) { gFt[a][b] = float(out[a][b]); tau[a][b] = float(td[a][b]); }
+    gmu += float(m);
+    glam += float(l);
+    galpha += float(al);
+}
+
+// ---------------------------------------------------------------------------
+// Quadratic B-spline stencil (MLS-MPM, Hu et al. 2018)
+// ---------------------------------------------------------------------------
+struct Stencil {
+    int base[3];
+    float fx[3];
+    float w[3][3];
+    float dw[3][3];   // derivative in x (already times inv_dx)
+};
+
+// Returns false if x is outside [dx, (res-2) dx) or not finite; base is then
+// clamped so that every access stays inside the grid.
+__device__ __forceinline__ bool make_stencil(const InstDev& I, const float (&x)[3], Stencil& st) {
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float X = x[a] * I.inv_dx;
+        ok = ok && (X >= 1.0f) && (X < float(I.res[a] - 2));
+        int b = __float2int_rd(X - 0.5f);
+        const int bc = min(max(b, 0), I.res[a] - 3);
+        ok = ok && (b == bc);
+        b = bc;
+        st.base[a] = b;
+        const float f = X - float(b);
+        st.fx[a] = f;
+        const float t0 = 1.5f - f, t1 = f - 1.0f, t2 = f - 0.5f;
+        st.w[a][0] = 0.5f * t0 * t0;
+        st.w[a][1] = 0.75f - t1 * t1;
+        st.w[a][2] = 0.5f * t2 * t2;
+        st.dw[a][0] = -t0 * I.inv_dx;
+        st.dw[a][1] = -2.0f * t1 * I.inv_dx;
+        st.dw[a][2] = t2 * I.inv_dx;
+    }
+    return ok;
+}
+
+// blocked grid layout: 4x4x4 nodes per block, blocks in (x, y, z) row-major
+__device__ __forceinline__ void node_offsets(const InstDev& I, const Stencil& st, int (&ox)[3], int (&oy)[3],
+                                             int (&oz)[3]) {
+    const int sx = I.nb[1] * I.nb[2] * 64, sy = I.nb[2] * 64;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int ix = st.base[0] + a, iy = st.base[1] + a, iz = st.base[2] + a;
+        ox[a] = (ix >> 2) * sx + (ix & 3) * 16;
+        oy[a] = (iy >> 2) * sy + (iy & 3) * 4;
+        oz[a] = (iz >> 2) * 64 + (iz & 3);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shovel: box SDF contact with Coulomb friction (Sec. III-A, collision)
+// ---------------------------------------------------------------------------
+struct Pose {
+    float c[3], psi, cd[3], psid;
+};
+
+__device__ __forceinline__ Pose load_pose(const InstDev& I, int substep) {
+    Pose P;
+    if (I.n_poses <= 0) {
+        P.c[0] = P.c[1] = P.c[2] = -1e6f;
+        P.psi = 0.0f;
+        P.cd[0] = P.cd[1] = P.cd[2] = 0.0f;
+        P.psid = 0.0f;
+        return P;
+    }
+    const bool past = substep >= I.n_poses;
+    const int s = past ? I.n_poses - 1 : substep;
+    const float* p = I.poses + 8 * s;
+    P.c[0] = p[0]; P.c[1] = p[1]; P.c[2] = p[2]; P.psi = p[3];
+    P.cd[0] = past ? 0.0f : p[4];
+    P.cd[1] = past ? 0.0f : p[5];
+    P.cd[2] = past ? 0.0f : p[6];
+    P.psid = past ? 0.0f : p[7];
+    return P;
+}
+
+// inside test; on success n (world) and nl (local) face normals
+__device__ __forceinline__ bool shovel_inside(const InstDev& I, const Pose& P, float cs, float sn, const float (&q)[3],
+                                              float (&n)[3], float (&nl)[3]) {
+    const float r0 = q[0] - P.c[0], r1 = q[1] - P.c[1], r2 = q[2] - P.c[2];
+    const float l0 = cs * r0 - sn * r1;
+    const float l1 = sn * r0 + cs * r1 - I.sh[1];
+    const float l2 = r2;
+    const float d0 = fabsf(l0) - I.sh[0], d1 = fabsf(l1) - I.sh[1], d2 = fabsf(l2) - I.sh[2];
+    if (!(d0 < 0.0f && d1 < 0.0f && d2 < 0.0f)) return false;
+    int a = 0;
+    float dm = d0;
+    if (d1 > dm) { a = 1; dm = d1; }
+    if (d2 > dm) { a = 2; }
+    nl[0] = nl[1] = nl[2] = 0.0f;
+    const float lv = (a == 0) ? l0 : ((a == 1) ? l1 : l2);
+    nl[a] = lv >= 0.0f ? 1.0f : -1.0f;
+    n[0] = cs * nl[0] + sn * nl[1];
+    n[1] = -sn * nl[0] + cs * nl[1];
+    n[2] = nl[2];
+    return true;
+}
+
+__device__ __forceinline__ void shovel_project(const InstDev& I, const Pose& P, float cs, float sn, const float (&q)[3],
+                                               float (&v)[3]) {
+    float n[3], nl[3];
+    if (!shovel_inside(I, P, cs, sn, q, n, nl)) return;
+    const float r0 = q[0] - P.c[0], r1 = q[1] - P.c[1];
+    const float vs0 = P.cd[0] + P.psid * r1, vs1 = P.cd[1] - P.psid * r0, vs2 = P.cd[2];
+    const float u0 = v[0] - vs0, u1 = v[1] - vs1, u2 = v[2] - vs2;
+    const float un = u0 * n[0] + u1 * n[1] + u2 * n[2];
+    if (un >= 0.0f) return;
+    const float t0 = u0 - un * n[0], t1 = u1 - un * n[1], t2 = u2 - un * n[2];
+    const float L = sqrtf(t0 * t0 + t1 * t1 + t2 * t2);
+    float f = 0.0f;
+    if (L > 0.0f) f = fmaxf(0.0f, 1.0f + I.friction * un / L);
+    v[0] = vs0 + f * t0;
+    v[1] = vs1 + f * t1;
+    v[2] = vs2 + f * t2;
+}
+
+// reverse of shovel_project: g (adjoint of the output) -> adds to gv, gq, gp[8]
+__device__ __forceinline__ void shovel_project_adj(const InstDev& I, const Pose& P, float cs, float sn,
+                                                   const float (&q)[3], const float (&v)[3], const float (&g)[3],
+                                                   float (&gv)[3], float (&gq)[3], float (&gp)[8]) {
+    float n[3], nl[3];
+    if (!shovel_inside(I, P, cs, sn, q, n, nl)) {
+        gv[0] += g[0]; gv[1] += g[1]; gv[2] += g[2];
+        return;
+    }
+    const float r0 = q[0] - P.c[0], r1 = q[1] - P.c[1];
+    const float vs0 = P.cd[0] + P.psid * r1, vs1 = P.cd[1] - P.psid * r0, vs2 = P.cd[2];
+    const float u[3] = {v[0] - vs0, v[1] - vs1, v[2] - vs2};
+    const float un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+    if (un >= 0.0f) {
+        gv[0] += g[0]; gv[1] += g[1]; gv[2] += g[2];
+        return;
+    }
+    const float ut[3] = {u[0] - un * n[0], u[1] - un * n[1], u[2] - un * n[2]};
+    const float L = sqrtf(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+    float gvs[3] = {g[0], g[1], g[2]};
+    float gu[3] = {0.0f, 0.0f, 0.0f}, gn[3] = {0.0f, 0.0f, 0.0f};
+    const float f = L > 0.0f ? 1.0f + I.friction * un / L : 0.0f;
+    if (L > 0.0f && f > 0.0f) {
+        const float gdot = g[0] * ut[0] + g[1] * ut[1] + g[2] * ut[2];
+        const float k = gdot * I.friction * un / (L * L * L);
+        float gut[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) gut[a] = f * g[a] - k * ut[a];
+        float gun = gdot * I.friction / L;
+        const float gutn = gut[0] * n[0] + gut[1] * n[1] + gut[2] * n[2];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            gu[a] += gut[a];
+            gn[a] -= un * gut[a];
+        }
+        gun -= gutn;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            gu[a] += gun * n[a];
+            gn[a] += gun * u[a];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        gv[a] += gu[a];
+        gvs[a] -= gu[a];
+    }
+    gp[4] += gvs[0];
+    gp[5] += gvs[1];
+    gp[6] += gvs[2];
+    gp[7] += gvs[0] * r1 - gvs[1] * r0;
+    const float gr0 = -P.psid * gvs[1], gr1 = P.psid * gvs[0];
+    const float dn0 = -sn * nl[0] + cs * nl[1], dn1 = -cs * nl[0] - sn * nl[1];
+    gp[3] += gn[0] * dn0 + gn[1] * dn1;
+    gq[0] += gr0;
+    gq[1] += gr1;
+    gp[0] -= gr0;
+    gp[1] -= gr1;
+}
+
+__device__ __forceinline__ float clipf(float g, float c) { return fminf(fmaxf(g, -c), c); }
+
+// ---------------------------------------------------------------------------
+// FP64 block reduction of `NV` values per thread into dst (atomicAdd)
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_reduce_add(double (&v)[NV], double* dst, double* sred /* [NV*32] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; k++) sred[k * 32 + warp] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            double x = lane < nw ? sred[k * 32 + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0 && x != 0.0) atomicAdd(dst + k, x);
+        }
+    }
+}
+
+}  // namespace mpm

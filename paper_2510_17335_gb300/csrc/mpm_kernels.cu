@@ -1,0 +1,702 @@
+// Kernels of the MLS-MPM sand substep (Algorithm 1 of DDBot, arXiv
+// 2510.17335) and of its adjoint, for sm_103a.
+//
+// Forward substep (3 launches, all instances of a batch in each):
+//   k_p2g   particle: trial F, SVD, Drucker-Prager return, Kirchhoff stress,
+//           APIC scatter of (m, mv) into the blocked grid; marks grid blocks
+//   k_grid  grid block (one warp): v = mv/m + dt g, walls, shovel contact
+//   k_g2p   particle: APIC gather of v and C, particle contact, advection
+// Adjoint substep (4 launches): k_g2p_bwd (scatter into the grid adjoint),
+// k_grid_bwd, k_p2g_bwd (gather, constitutive adjoint, parameter sums),
+// k_grid_clear.
+#include <cuda_runtime.h>
+
+#include "mpm_device.cuh"
+#include "mpm_launch.h"
+
+namespace mpm {
+
+__device__ __forceinline__ float ld(const float* s, long long ncap, int comp, long long p) {
+    return s[comp * ncap + p];
+}
+
+// mark the (up to 8) grid blocks a stencil touches
+__device__ __forceinline__ void mark_blocks(const InstDev& I, const Stencil& st, unsigned char* flags) {
+    const int b0x = st.base[0] >> 2, b1x = (st.base[0] + 2) >> 2;
+    const int b0y = st.base[1] >> 2, b1y = (st.base[1] + 2) >> 2;
+    const int b0z = st.base[2] >> 2, b1z = (st.base[2] + 2) >> 2;
+    for (int bx = b0x; bx <= b1x; bx++)
+        for (int by = b0y; by <= b1y; by++)
+            for (int bz = b0z; bz <= b1z; bz++) {
+                unsigned char* f = flags + I.blk_off + (bx * I.nb[1] + by) * I.nb[2] + bz;
+                if (*f == 0) *f = 1;
+            }
+}
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kChunk) k_p2g(StepArgs a) {
+    const int inst = a.chunk_inst[blockIdx.x];
+    const InstDev& I = a.inst[inst];
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (p - I.pbeg >= I.n) return;
+    const long long N = a.ncap;
+    float x[3], v[3], C[3][3], F[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        x[k] = ld(a.sin, N, kX + k, p);
+        v[k] = ld(a.sin, N, kV + k, p);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            C[r][c] = ld(a.sin, N, kC + 3 * r + c, p);
+            F[r][c] = ld(a.sin, N, kF + 3 * r + c, p);
+        }
+    // trial deformation gradient (I + dt C) F
+    float Ft[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            Ft[r][c] = F[r][c] + I.dt * (C[r][0] * F[0][c] + C[r][1] * F[1][c] + C[r][2] * F[2][c]);
+    float Fn[3][3], tau[3][3];
+    if (constitutive(Ft, I.mu, I.lam, I.beta, I.smin, Fn, tau)) atomicAdd(a.fp64_count, 1ull);
+    bool finite = true;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            a.sout[(kF + 3 * r + c) * N + p] = Fn[r][c];
+            finite = finite && isfinite(Fn[r][c]);
+        }
+    if (!finite) atomicOr(a.status, kStatusNonFinite);
+    // affine momentum: stress term of MLS-MPM plus APIC
+    float A[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) A[r][c] = I.stress_scale * tau[r][c] + I.mp * C[r][c];
+    Stencil st;
+    if (!make_stencil(I, x, st)) atomicOr(a.status, kStatusDomain);
+    int ox[3], oy[3], oz[3];
+    node_offsets(I, st, ox, oy, oz);
+    float mv[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) mv[k] = I.mp * v[k];
+    // A d with d = (o - f) dx, built per axis
+    float4* acc = a.acc + I.node_off;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const float dxi = (float(i) - st.fx[0]) * I.dx;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float dyj = (float(j) - st.fx[1]) * I.dx;
+            const float wij = st.w[0][i] * st.w[1][j];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float dzk = (float(k) - st.fx[2]) * I.dx;
+                const float W = wij * st.w[2][k];
+                float4 val;
+                val.x = W * I.mp;
+                val.y = W * (mv[0] + A[0][0] * dxi + A[0][1] * dyj + A[0][2] * dzk);
+                val.z = W * (mv[1] + A[1][0] * dxi + A[1][1] * dyj + A[1][2] * dzk);
+                val.w = W * (mv[2] + A[2][0] * dxi + A[2][1] * dyj + A[2][2] * dzk);
+                atomicAdd(acc + ox[i] + oy[j] + oz[k], val);
+            }
+        }
+    }
+    mark_blocks(I, st, a.flags);
+}
+
+// velocity update of one node (gravity, walls); returns false for empty nodes
+__device__ __forceinline__ void grid_node(const InstDev& I, const Pose& P, float cs, float sn, int ix, int iy, int iz,
+                                          float4 acc, float (&vg)[3], float (&mask)[3]) {
+    const float inv_m = 1.0f / acc.x;
+    vg[0] = acc.y * inv_m + I.dt * I.g[0];
+    vg[1] = acc.z * inv_m + I.dt * I.g[1];
+    vg[2] = acc.w * inv_m + I.dt * I.g[2];
+    const int idx[3] = {ix, iy, iz};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        mask[d] = 1.0f;
+        if (idx[d] < I.bound && vg[d] < 0.0f) { vg[d] = 0.0f; mask[d] = 0.0f; }
+        if (idx[d] > I.res[d] - I.bound && vg[d] > 0.0f) { vg[d] = 0.0f; mask[d] = 0.0f; }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_grid(StepArgs a) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= a.n_blocks) return;
+    if (a.flags[gw] == 0) return;
+    const InstDev& I = a.inst[a.block_inst[gw]];
+    const int lb = gw - I.blk_off;
+    const int bz = lb % I.nb[2], by = (lb / I.nb[2]) % I.nb[1], bx = lb / (I.nb[1] * I.nb[2]);
+    const Pose P = load_pose(I, a.substep);
+    float sn, cs;
+    sincosf(P.psi, &sn, &cs);
+    const long long base = I.node_off + (long long)lb * 64;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int nd = lane + 32 * h;
+        const int ix = bx * 4 + (nd >> 4), iy = by * 4 + ((nd >> 2) & 3), iz = bz * 4 + (nd & 3);
+        const float4 acc = a.acc[base + nd];
+        float4 out = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (acc.x > 0.0f) {
+            float vg[3], mask[3];
+            grid_node(I, P, cs, sn, ix, iy, iz, acc, vg, mask);
+            if (I.shovel_on) {
+                const float q[3] = {ix * I.dx, iy * I.dx, iz * I.dx};
+                shovel_project(I, P, cs, sn, q, vg);
+            }
+            out = make_float4(vg[0], vg[1], vg[2], acc.x);
+        }
+        a.vout[base + nd] = out;
+        if (!a.keep_grid) a.acc[base + nd] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    if (!a.keep_grid && lane == 0) a.flags[gw] = 0;
+}
+
+__global__ void __launch_bounds__(kChunk) k_g2p(StepArgs a) {
+    const int inst = a.chunk_inst[blockIdx.x];
+    const InstDev& I = a.inst[inst];
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (p - I.pbeg >= I.n) return;
+    const long long N = a.ncap;
+    float x[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) x[k] = ld(a.sin, N, kX + k, p);
+    Stencil st;
+    make_stencil(I, x, st);
+    int ox[3], oy[3], oz[3];
+    node_offsets(I, st, ox, oy, oz);
+    const float4* vg = a.vout + I.node_off;
+    float v[3] = {0.0f, 0.0f, 0.0f}, B[3][3] = {{0.0f}};
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const float di = float(i) - st.fx[0];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float dj = float(j) - st.fx[1];
+            const float wij = st.w[0][i] * st.w[1][j];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float dk = float(k) - st.fx[2];
+                const float W = wij * st.w[2][k];
+                const float4 g = __ldg(vg + ox[i] + oy[j] + oz[k]);
+                v[0] += W * g.x;
+                v[1] += W * g.y;
+                v[2] += W * g.z;
+                B[0][0] += W * g.x * di; B[0][1] += W * g.x * dj; B[0][2] += W * g.x * dk;
+                B[1][0] += W * g.y * di; B[1][1] += W * g.y * dj; B[1][2] += W * g.y * dk;
+                B[2][0] += W * g.z * di; B[2][1] += W * g.z * dj; B[2][2] += W * g.z * dk;
+            }
+        }
+    }
+    // C = 4/dx^2 sum W v d^T with d = (o - f) dx
+    const float cscale = 4.0f * I.inv_dx;
+    if (I.pcoll && I.shovel_on) {
+        const Pose P = load_pose(I, a.substep);
+        float sn, cs;
+        sincosf(P.psi, &sn, &cs);
+        shovel_project(I, P, cs, sn, x, v);
+    }
+    float xn[3];
+    bool finite = true;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        xn[k] = x[k] + I.dt * v[k];
+        finite = finite && isfinite(xn[k]);
+    }
+    bool inside = true;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float X = xn[k] * I.inv_dx;
+        inside = inside && (X >= 1.0f) && (X < float(I.res[k] - 2));
+    }
+    if (!finite) atomicOr(a.status, kStatusNonFinite);
+    if (!inside) atomicOr(a.status, kStatusDomain);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        a.sout[(kX + k) * N + p] = xn[k];
+        a.sout[(kV + k) * N + p] = v[k];
+    }
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) a.sout[(kC + 3 * r + c) * N + p] = cscale * B[r][c];
+}
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kChunk) k_g2p_bwd(AdjArgs A) {
+    __shared__ double sred[8 * 32];
+    const StepArgs& a = A.f;
+    const int inst = a.chunk_inst[blockIdx.x];
+    const InstDev& I = a.inst[inst];
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    const bool active = p - I.pbeg < I.n;
+    const long long N = a.ncap;
+    float gp[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (active) {
+        float x[3], gx[3], gv[3], gC[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            x[k] = ld(a.sin, N, kX + k, p);
+            gx[k] = A.adj[(kX + k) * N + p];
+            gv[k] = A.adj[(kV + k) * N + p];
+            if (a.clip > 0.f) { gx[k] = clipf(gx[k], a.clip); gv[k] = clipf(gv[k], a.clip); }
+        }
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) gC[r][c] = A.adj[(kC + 3 * r + c) * N + p];
+        Stencil st;
+        make_stencil(I, x, st);
+        int ox[3], oy[3], oz[3];
+        node_offsets(I, st, ox, oy, oz);
+        const float4* vg = a.vout + I.node_off;
+        // adjoint of the advection x' = x + dt v'
+        float gvn[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) gvn[k] = gv[k] + I.dt * gx[k];
+        if (I.pcoll && I.shovel_on) {
+            // the contact needs the pre-contact G2P velocity
+            float v[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++)
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        const float W = st.w[0][i] * st.w[1][j] * st.w[2][k];
+                        const float4 g = __ldg(vg + ox[i] + oy[j] + oz[k]);
+                        v[0] += W * g.x; v[1] += W * g.y; v[2] += W * g.z;
+                    }
+            const Pose P = load_pose(I, a.substep);
+            float sn, cs;
+            sincosf(P.psi, &sn, &cs);
+            float g0[3] = {gvn[0], gvn[1], gvn[2]}, gq[3] = {0.f, 0.f, 0.f};
+            gvn[0] = gvn[1] = gvn[2] = 0.f;
+            shovel_project_adj(I, P, cs, sn, x, v, g0, gvn, gq, gp);
+            gx[0] += gq[0]; gx[1] += gq[1]; gx[2] += gq[2];
+        }
+        // adjoint of the APIC gather: scatter into the grid velocity adjoint
+        const float kap = 4.0f * I.inv_dx * I.inv_dx;
+        float4* ga = A.gacc + I.node_off;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const float wx = st.w[0][i], wy = st.w[1][j], wz = st.w[2][k];
+                    const float W = wx * wy * wz;
+                    const float gW[3] = {st.dw[0][i] * wy * wz, wx * st.dw[1][j] * wz, wx * wy * st.dw[2][k]};
+                    const float d[3] = {(float(i) - st.fx[0]) * I.dx, (float(j) - st.fx[1]) * I.dx,
+                                        (float(k) - st.fx[2]) * I.dx};
+                    const float4 g = __ldg(vg + ox[i] + oy[j] + oz[k]);
+                    const float vi[3] = {g.x, g.y, g.z};
+                    float Cd[3];
+#pragma unroll
+                    for (int r = 0; r < 3; r++) Cd[r] = gC[r][0] * d[0] + gC[r][1] * d[1] + gC[r][2] * d[2];
+                    float4 contrib;
+                    contrib.x = W * (gvn[0] + kap * Cd[0]);
+                    contrib.y = W * (gvn[1] + kap * Cd[1]);
+                    contrib.z = W * (gvn[2] + kap * Cd[2]);
+                    contrib.w = 0.f;
+                    atomicAdd(ga + ox[i] + oy[j] + oz[k], contrib);
+                    const float Wbar = vi[0] * (gvn[0] + kap * Cd[0]) + vi[1] * (gvn[1] + kap * Cd[1]) +
+                                       vi[2] * (gvn[2] + kap * Cd[2]);
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const float dbar = kap * W * (gC[0][c] * vi[0] + gC[1][c] * vi[1] + gC[2][c] * vi[2]);
+                        gx[c] += Wbar * gW[c] - dbar;
+                    }
+                }
+#pragma unroll
+        for (int k = 0; k < 3; k++) A.adj[(kX + k) * N + p] = gx[k];
+    }
+    if (I.pcoll && I.shovel_on) {
+        double gd[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) gd[k] = gp[k];
+        block_reduce_add<8>(gd, A.gpose + 8 * inst, sred);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
+    const StepArgs& a = A.f;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= a.n_blocks) return;
+    if (a.flags[gw] == 0) return;
+    const int inst = a.block_inst[gw];
+    const InstDev& I = a.inst[inst];
+    const int lb = gw - I.blk_off;
+    const int bz = lb % I.nb[2], by = (lb / I.nb[2]) % I.nb[1], bx = lb / (I.nb[1] * I.nb[2]);
+    const Pose P = load_pose(I, a.substep);
+    float sn, cs;
+    sincosf(P.psi, &sn, &cs);
+    const long long base = I.node_off + (long long)lb * 64;
+    float gp[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int nd = lane + 32 * h;
+        const int ix = bx * 4 + (nd >> 4), iy = by * 4 + ((nd >> 2) & 3), iz = bz * 4 + (nd & 3);
+        const float4 acc = a.acc[base + nd];
+        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (acc.x > 0.f) {
+            const float4 gin = A.gacc[base + nd];
+            float g[3] = {gin.x, gin.y, gin.z};
+            if (a.clip > 0.f) {
+#pragma unroll
+                for (int d = 0; d < 3; d++) g[d] = clipf(g[d], a.clip);
+            }
+            float vg[3], mask[3];
+            grid_node(I, P, cs, sn, ix, iy, iz, acc, vg, mask);
+            float gv[3] = {0.f, 0.f, 0.f};
+            if (I.shovel_on) {
+                const float q[3] = {ix * I.dx, iy * I.dx, iz * I.dx};
+                float gq[3] = {0.f, 0.f, 0.f};
+                shovel_project_adj(I, P, cs, sn, q, vg, g, gv, gq, gp);
+            } else {
+                gv[0] = g[0]; gv[1] = g[1]; gv[2] = g[2];
+            }
+            const float inv_m = 1.0f / acc.x;
+            float dot = 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                gv[d] *= mask[d];
+                if (a.clip > 0.f) gv[d] = clipf(gv[d], a.clip);
+            }
+            dot = gv[0] * acc.y + gv[1] * acc.z + gv[2] * acc.w;
+            float gm = -dot * inv_m * inv_m;
+            if (a.clip > 0.f) gm = clipf(gm, a.clip);
+            out = make_float4(gm, gv[0] * inv_m, gv[1] * inv_m, gv[2] * inv_m);
+        }
+        A.gacc[base + nd] = out;
+    }
+    if (I.shovel_on) {
+        // warp sum of the pose adjoint in FP64, one atomic per value and warp
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < 8; k++) any = any || (gp[k] != 0.f);
+        if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                double x = gp[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (lane == 0 && x != 0.0) atomicAdd(A.gpose + 8 * inst + k, x);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kChunk) k_p2g_bwd(AdjArgs A) {
+    __shared__ double sred[4 * 32];
+    const StepArgs& a = A.f;
+    const int inst = a.chunk_inst[blockIdx.x];
+    const InstDev& I = a.inst[inst];
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    const bool active = p - I.pbeg < I.n;
+    const long long N = a.ncap;
+    float gmu = 0.f, glam = 0.f, galpha = 0.f, gmp = 0.f;
+    if (active) {
+        float x[3], v[3], C[3][3], F[3][3], gx[3], gFn[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            x[k] = ld(a.sin, N, kX + k, p);
+            v[k] = ld(a.sin, N, kV + k, p);
+            gx[k] = A.adj[(kX + k) * N + p];
+        }
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                C[r][c] = ld(a.sin, N, kC + 3 * r + c, p);
+                F[r][c] = ld(a.sin, N, kF + 3 * r + c, p);
+                float g = A.adj[(kF + 3 * r + c) * N + p];
+                gFn[r][c] = a.clip > 0.f ? clipf(g, a.clip) : g;
+            }
+        float Ft[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                Ft[r][c] = F[r][c] + I.dt * (C[r][0] * F[0][c] + C[r][1] * F[1][c] + C[r][2] * F[2][c]);
+        Spectral<float> S;
+        constitutive_spectral<float>(Ft, I.mu, I.lam, I.beta, I.smin, S);
+        const bool fb = needs_fp64(S);
+        float Fn[3][3], tau[3][3];
+        if (!fb) spectral_outputs<float, float>(S, Fn, tau);
+        else {
+            constitutive_fp64(Ft, I.mu, I.lam, I.beta, I.smin, Fn, tau);
+        }
+        float Am[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) Am[r][c] = I.stress_scale * tau[r][c] + I.mp * C[r][c];
+        Stencil st;
+        make_stencil(I, x, st);
+        int ox[3], oy[3], oz[3];
+        node_offsets(I, st, ox, oy, oz);
+        const float4* ga = A.gacc + I.node_off;
+        float gv[3] = {0.f, 0.f, 0.f}, gA[3][3] = {{0.f}};
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const float wx = st.w[0][i], wy = st.w[1][j], wz = st.w[2][k];
+                    const float W = wx * wy * wz;
+                    const float gW[3] = {st.dw[0][i] * wy * wz, wx * st.dw[1][j] * wz, wx * wy * st.dw[2][k]};
+                    const float d[3] = {(float(i) - st.fx[0]) * I.dx, (float(j) - st.fx[1]) * I.dx,
+                                        (float(k) - st.fx[2]) * I.dx};
+                    const float4 g = ga[ox[i] + oy[j] + oz[k]];
+                    const float gm = g.x, gmv[3] = {g.y, g.z, g.w};
+                    float Wbar = gm * I.mp;
+#pragma unroll
+                    for (int r = 0; r < 3; r++) {
+                        const float Ad = Am[r][0] * d[0] + Am[r][1] * d[1] + Am[r][2] * d[2];
+                        Wbar += gmv[r] * (I.mp * v[r] + Ad);
+                        gv[r] += W * I.mp * gmv[r];
+                        gmp += W * gmv[r] * v[r];
+#pragma unroll
+                        for (int c = 0; c < 3; c++) gA[r][c] += W * gmv[r] * d[c];
+                    }
+                    gmp += W * gm;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const float dbar = W * (Am[0][c] * gmv[0] + Am[1][c] * gmv[1] + Am[2][c] * gmv[2]);
+                        gx[c] += Wbar * gW[c] - dbar;
+                    }
+                }
+        float gtau[3][3], gC[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                gtau[r][c] = I.stress_scale * gA[r][c];
+                gC[r][c] = I.mp * gA[r][c];
+                gmp += gA[r][c] * C[r][c];
+            }
+        float gFt[3][3];
+        if (!fb) {
+            constitutive_adjoint_spectral<float>(S, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, gFt, gmu, glam,
+                                                 galpha);
+        } else {
+            constitutive_adjoint_fp64(Ft, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, tau, gFt, gmu, glam, galpha);
+        }
+        // Ft = (I + dt C) F
+        float gF[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                gF[r][c] = gFt[r][c] + I.dt * (C[0][r] * gFt[0][c] + C[1][r] * gFt[1][c] + C[2][r] * gFt[2][c]);
+                gC[r][c] += I.dt * (gFt[r][0] * F[c][0] + gFt[r][1] * F[c][1] + gFt[r][2] * F[c][2]);
+            }
+        bool finite = true;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            A.adj[(kX + k) * N + p] = gx[k];
+            A.adj[(kV + k) * N + p] = gv[k];
+            finite = finite && isfinite(gx[k]) && isfinite(gv[k]);
+        }
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                A.adj[(kC + 3 * r + c) * N + p] = gC[r][c];
+                A.adj[(kF + 3 * r + c) * N + p] = gF[r][c];
+                finite = finite && isfinite(gF[r][c]) && isfinite(gC[r][c]);
+            }
+        if (!finite) atomicOr(a.status, kStatusNonFinite);
+    }
+    double gd[4] = {gmu, glam, galpha, gmp};
+    block_reduce_add<4>(gd, A.gmat + 4 * inst, sred);
+}
+
+__global__ void __launch_bounds__(256) k_grid_clear(AdjArgs A) {
+    const StepArgs& a = A.f;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= a.n_blocks) return;
+    if (a.flags[gw] == 0) return;
+    const InstDev& I = a.inst[a.block_inst[gw]];
+    const long long base = I.node_off + (long long)(gw - I.blk_off) * 64;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    A.gacc[base + lane] = z;
+    A.gacc[base + lane + 32] = z;
+    a.acc[base + lane] = z;
+    a.acc[base + lane + 32] = z;
+    __syncwarp();
+    if (lane == 0) a.flags[gw] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// layout conversion, loss, seeding
+// ---------------------------------------------------------------------------
+// external interleaved arrays (x[3e+k], M[9e+k]) <-> internal SoA slots
+__global__ void k_state_from_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* x,
+                                 const float* v, const float* C, const float* F, float* s) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nslots) return;
+    const int e = ext_of_slot[p];
+    const bool on = e >= 0;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        s[(kX + k) * ncap + p] = (on && x) ? x[3LL * e + k] : 0.5f;
+        s[(kV + k) * ncap + p] = (on && v) ? v[3LL * e + k] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        s[(kC + k) * ncap + p] = (on && C) ? C[9LL * e + k] : 0.f;
+        s[(kF + k) * ncap + p] = (on && F) ? F[9LL * e + k] : ((k % 4 == 0) ? 1.f : 0.f);
+    }
+}
+
+// adjoint seed: x and v adjoints from external arrays (or 0), C and F 0
+__global__ void k_adj_from_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* gx,
+                               const float* gv, float* adj) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nslots) return;
+    const int e = ext_of_slot[p];
+    const bool on = e >= 0;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        adj[(kX + k) * ncap + p] = (on && gx) ? gx[3LL * e + k] : 0.f;
+        adj[(kV + k) * ncap + p] = (on && gv) ? gv[3LL * e + k] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 18; k++) adj[(kC + k) * ncap + p] = 0.f;
+}
+
+__global__ void k_state_to_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* s, float* x,
+                               float* v, float* C, float* F) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nslots) return;
+    const int e = ext_of_slot[p];
+    if (e < 0) return;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (x) x[3LL * e + k] = s[(kX + k) * ncap + p];
+        if (v) v[3LL * e + k] = s[(kV + k) * ncap + p];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        if (C) C[9LL * e + k] = s[(kC + k) * ncap + p];
+        if (F) F[9LL * e + k] = s[(kF + k) * ncap + p];
+    }
+}
+
+__global__ void __launch_bounds__(kChunk) k_loss_mse(const InstDev* inst, const int* chunk_inst, long long ncap,
+                                                    const int* ext_of_slot, const float* s, const float* target,
+                                                    float* dldx, double* loss) {
+    __shared__ double sred[32];
+    const int ii = chunk_inst[blockIdx.x];
+    const InstDev& I = inst[ii];
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    double l = 0.0;
+    if (p - I.pbeg < I.n) {
+        const int e = ext_of_slot[p];
+        const float inv_n = 1.0f / float(I.n);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float d = s[(kX + k) * ncap + p] - target[3LL * e + k];
+            l += double(d) * double(d);
+            if (dldx) dldx[3LL * e + k] = 2.0f * d * inv_n;
+        }
+        l /= double(I.n);
+    }
+    double v1[1] = {l};
+    block_reduce_add<1>(v1, loss + ii, sred);
+}
+
+// total grid mass per instance after the last grid update (vout.w = m)
+__global__ void __launch_bounds__(256) k_grid_mass(const InstDev* inst, const int* block_inst, int n_blocks,
+                                                   const float4* vout, double* mass) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= n_blocks) return;
+    const int ii = block_inst[gw];
+    const InstDev& I = inst[ii];
+    const long long base = I.node_off + (long long)(gw - I.blk_off) * 64;
+    double m = (double)vout[base + lane].w + (double)vout[base + lane + 32].w;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
+    if (lane == 0 && m != 0.0) atomicAdd(mass + ii, m);
+}
+
+}  // namespace mpm
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+namespace mpm {
+
+static inline int grid_ctas(int n_blocks) { return (n_blocks * 32 + 255) / 256; }
+
+cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
+    const StepArgs& a = A.f;
+    const bool particle_kernel = id == KernelId::P2G || id == KernelId::G2P || id == KernelId::G2PBwd ||
+                                 id == KernelId::P2GBwd;
+    if ((particle_kernel && a.n_chunks <= 0) || (!particle_kernel && a.n_blocks <= 0)) return cudaSuccess;
+    switch (id) {
+        case KernelId::P2G: k_p2g<<<a.n_chunks, kChunk, 0, s>>>(a); break;
+        case KernelId::Grid: k_grid<<<grid_ctas(a.n_blocks), 256, 0, s>>>(a); break;
+        case KernelId::G2P: k_g2p<<<a.n_chunks, kChunk, 0, s>>>(a); break;
+        case KernelId::G2PBwd: k_g2p_bwd<<<a.n_chunks, kChunk, 0, s>>>(A); break;
+        case KernelId::GridBwd: k_grid_bwd<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
+        case KernelId::P2GBwd: k_p2g_bwd<<<a.n_chunks, kChunk, 0, s>>>(A); break;
+        case KernelId::GridClear: k_grid_clear<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_from_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* x,
+                                  const float* v, const float* C, const float* F, float* s, cudaStream_t st) {
+    if (nslots == 0) return cudaSuccess;
+    k_state_from_ext<<<(unsigned)((nslots + 255) / 256), 256, 0, st>>>(ncap, nslots, ext_of_slot, x, v, C, F, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_from_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* gx,
+                                const float* gv, float* adj, cudaStream_t st) {
+    if (nslots == 0) return cudaSuccess;
+    k_adj_from_ext<<<(unsigned)((nslots + 255) / 256), 256, 0, st>>>(ncap, nslots, ext_of_slot, gx, gv, adj);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_to_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* s, float* x,
+                                float* v, float* C, float* F, cudaStream_t st) {
+    if (nslots == 0) return cudaSuccess;
+    k_state_to_ext<<<(unsigned)((nslots + 255) / 256), 256, 0, st>>>(ncap, nslots, ext_of_slot, s, x, v, C, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_mass(const InstDev* inst, const int* block_inst, int n_blocks, const float4* vout,
+                             double* mass, cudaStream_t st) {
+    if (n_blocks == 0) return cudaSuccess;
+    k_grid_mass<<<grid_ctas(n_blocks), 256, 0, st>>>(inst, block_inst, n_blocks, vout, mass);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss_mse(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap,
+                            const int* ext_of_slot, const float* s, const float* target, float* dldx, double* loss,
+                            cudaStream_t st) {
+    if (n_chunks == 0) return cudaSuccess;
+    k_loss_mse<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, ncap, ext_of_slot, s, target, dldx, loss);
+    return cudaGetLastError();
+}
+
+}  // namespace mpm

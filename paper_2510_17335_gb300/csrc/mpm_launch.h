@@ -1,0 +1,26 @@
+// Host-side launchers of the library's kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mpm_types.h"
+
+namespace mpm {
+
+enum class KernelId : int { P2G = 0, Grid, G2P, G2PBwd, GridBwd, P2GBwd, GridClear, Count };
+
+// one substep kernel; forward kernels read only A.f
+cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s);
+cudaError_t launch_state_from_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* x,
+                                  const float* v, const float* C, const float* F, float* s, cudaStream_t st);
+cudaError_t launch_adj_from_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* gx,
+                                const float* gv, float* adj, cudaStream_t st);
+cudaError_t launch_state_to_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* s, float* x,
+                                float* v, float* C, float* F, cudaStream_t st);
+cudaError_t launch_grid_mass(const InstDev* inst, const int* block_inst, int n_blocks, const float4* vout,
+                             double* mass, cudaStream_t st);
+cudaError_t launch_loss_mse(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap,
+                            const int* ext_of_slot, const float* s, const float* target, float* dldx, double* loss,
+                            cudaStream_t st);
+
+
+}  // namespace mpm

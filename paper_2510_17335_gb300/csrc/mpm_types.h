@@ -1,0 +1,67 @@
+// Types shared by the host side of the library and its kernels.
+#pragma once
+#include <stdint.h>
+
+namespace mpm {
+
+constexpr int kChunk = 256;        // particles per CTA in particle kernels; instances are padded to it
+constexpr int kStateComps = 24;    // x 3, v 3, C 9, F 9 (structure of arrays)
+constexpr int kX = 0, kV = 3, kC = 6, kF = 15;
+
+// status bits written by kernels
+constexpr int kStatusDomain = 1;
+constexpr int kStatusNonFinite = 2;
+
+// One instance, as the kernels see it (device memory, read-only in kernels).
+struct InstDev {
+    int res[3];
+    int nb[3];              // 4x4x4 blocks per axis
+    int bound;
+    int shovel_on;
+    int pcoll;
+    int n_poses;
+    int n;                  // particles
+    int blk_off;            // first grid block of this instance
+    long long pbeg;         // first particle slot
+    long long node_off;     // first node (blocked layout)
+    float dx, inv_dx, dt;
+    float g[3];
+    float mu, lam, alpha, beta;   // beta = (3 lam + 2 mu) / (2 mu) * alpha
+    float mp, vol;
+    float stress_scale;     // -dt * vol * 4 / dx^2
+    float friction;
+    float sh[3];
+    float smin;
+    const float* poses;     // n_poses * 8: tip xyz, psi, tip velocity, psi rate
+};
+
+// Arguments of one substep's kernels (passed by value).
+struct StepArgs {
+    const InstDev* inst;
+    const int* chunk_inst;  // particle chunk -> instance
+    const int* block_inst;  // grid block -> instance
+    long long ncap;         // stride of a state component
+    int n_chunks;
+    int n_blocks;
+    int substep;            // index into the pose tables
+    const float* sin;       // state at the start of the substep [24][ncap]
+    float* sout;            // state at the end (may equal sin)
+    float4* acc;            // P2G accumulators (m, mv) of this substep
+    float4* vout;           // grid velocity after the update (xyz), mass (w)
+    unsigned char* flags;   // grid blocks touched this substep
+    int keep_grid;          // 1: the grid kernel leaves acc/flags for the backward
+    int* status;
+    unsigned long long* fp64_count;
+    float clip;             // > 0: clip adjoints to [-clip, clip]
+};
+
+// Arguments of one substep's adjoint kernels.
+struct AdjArgs {
+    StepArgs f;             // the forward substep being reversed (sin = state_k)
+    float* adj;             // adjoint of the state [24][ncap], in place: k+1 -> k
+    float4* gacc;           // grid adjoint buffer (zero on entry for touched blocks)
+    double* gmat;           // n_inst * 4: d/d(mu, lambda, alpha, m_p)
+    double* gpose;          // n_inst * 8: adjoint of this substep's pose
+};
+
+}  // namespace mpm

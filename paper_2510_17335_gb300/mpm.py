@@ -1,0 +1,334 @@
+"""Thin ctypes binding of libmpm_gb300.so (include/mpm.h).
+
+Functions carry the C names and do argument marshalling only: numpy arrays
+are passed as host pointers, torch CUDA tensors as device pointers. Every
+step of the simulation runs in the library's CUDA kernels; there is no CPU
+path. ``lib()`` raises if the library is missing or cannot be loaded.
+
+``Simulation`` is a small convenience owner of one handle (creation from a
+list of workloads, state and gradient accessors).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpm_gb300.so")
+
+MPM_OK = 0
+ERRORS = {
+    -1: "MPM_ERR_INVALID_ARG", -2: "MPM_ERR_OOM", -3: "MPM_ERR_CUDA", -4: "MPM_ERR_OUT_OF_DOMAIN",
+    -5: "MPM_ERR_NON_FINITE", -6: "MPM_ERR_NO_RECORD", -7: "MPM_ERR_TIMEOUT", -8: "MPM_ERR_NO_DEVICE",
+}
+
+
+class MpmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib().mpm_error_string(code).decode() if _lib is not None else ERRORS.get(code, "?")
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({msg})")
+
+
+class mpm_material(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("rho", ctypes.c_double),
+                ("phi_deg", ctypes.c_double)]
+
+
+class mpm_config(ctypes.Structure):
+    _fields_ = [("res", ctypes.c_int * 3), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+                ("gravity", ctypes.c_double * 3), ("bound", ctypes.c_int), ("particle_volume", ctypes.c_double),
+                ("friction", ctypes.c_double), ("particle_collision", ctypes.c_int),
+                ("shovel_half", ctypes.c_double * 3), ("shovel_on", ctypes.c_int)]
+
+
+class mpm_options(ctypes.Structure):
+    _fields_ = [("checkpoint_every", ctypes.c_int), ("clip_grads", ctypes.c_int), ("clip_value", ctypes.c_double),
+                ("sigma_min", ctypes.c_double), ("sort_every", ctypes.c_int)]
+
+
+class mpm_skill(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double * 6), ("v_lin", ctypes.c_double), ("v_ang", ctypes.c_double),
+                ("substeps_per_action", ctypes.c_int), ("start_pose", ctypes.c_double * 4)]
+
+
+class mpm_info_t(ctypes.Structure):
+    _fields_ = [("n_inst", ctypes.c_int), ("n_particles", ctypes.c_int64), ("substep", ctypes.c_int64),
+                ("recorded", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("fp64_fallbacks", ctypes.c_int64)]
+
+
+_vp, _dp, _fp, _ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_int
+_lib = None
+
+EXPORTS = {
+    "mpm_create": (_ip, [_ip, ctypes.POINTER(mpm_config), ctypes.POINTER(mpm_material), ctypes.POINTER(ctypes.c_int64),
+                         _fp, ctypes.POINTER(mpm_options), ctypes.POINTER(_vp)]),
+    "mpm_set_material": (_ip, [_vp, _ip, ctypes.POINTER(mpm_material)]),
+    "mpm_set_shovel_actions": (_ip, [_vp, _ip, _dp, _ip, _dp, _ip]),
+    "mpm_set_shovel_trajectory": (_ip, [_vp, _ip, ctypes.POINTER(mpm_skill)]),
+    "mpm_num_actions": (_ip, [_vp, _ip]),
+    "mpm_reset": (_ip, [_vp]),
+    "mpm_set_state": (_ip, [_vp, _fp, _fp, _fp, _fp, _ip]),
+    "mpm_get_state": (_ip, [_vp, _fp, _fp, _fp, _fp, _ip]),
+    "mpm_forward": (_ip, [_vp, _ip, _ip]),
+    "mpm_loss_mse": (_ip, [_vp, _fp, _dp, _fp, _ip]),
+    "mpm_backward": (_ip, [_vp, _fp, _fp, _ip, _dp, _dp]),
+    "mpm_get_state_grad": (_ip, [_vp, _fp, _fp, _fp, _fp, _ip]),
+    "mpm_get_action_grad": (_ip, [_vp, _ip, _dp, _dp]),
+    "mpm_set_stream": (_ip, [_vp, _vp]),
+    "mpm_synchronize": (_ip, [_vp]),
+    "mpm_get_info": (_ip, [_vp, ctypes.POINTER(mpm_info_t)]),
+    "mpm_grid_mass": (_ip, [_vp, _dp]),
+    "mpm_set_substep": (_ip, [_vp, ctypes.c_int64]),
+    "mpm_profile": (_ip, [_vp, _ip]),
+    "mpm_profile_read": (_ip, [_vp, _ip, _dp, ctypes.POINTER(ctypes.c_int64)]),
+    "mpm_kernel_name": (ctypes.c_char_p, [_ip]),
+    "mpm_destroy": (None, [_vp]),
+    "mpm_error_string": (ctypes.c_char_p, [_ip]),
+    "mpm_version": (_ip, []),
+}
+
+
+def lib():
+    """Load libmpm_gb300.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2510_17335_gb300.build` "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code: int, where: str) -> None:
+    if code != MPM_OK:
+        raise MpmError(code, where)
+
+
+# ---------------------------------------------------------------------------
+# pointer marshalling
+# ---------------------------------------------------------------------------
+def _ptr(a, device: bool):
+    """(pointer, keepalive) for a float32 numpy array (host) or torch tensor (device)."""
+    if a is None:
+        return None, None
+    if device:
+        import torch
+        assert isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float32 and a.is_contiguous()
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    return arr.ctypes.data_as(ctypes.c_void_p), arr
+
+
+def _is_device(*arrays) -> bool:
+    for a in arrays:
+        if a is not None and hasattr(a, "is_cuda"):
+            return bool(a.is_cuda)
+    return False
+
+
+def make_config(res, dx, dt, particle_volume, gravity=(0.0, -9.8, 0.0), bound=3, friction=0.5,
+                particle_collision=1, shovel_half=(0.01, 0.075, 0.1), shovel_on=1) -> mpm_config:
+    c = mpm_config()
+    c.res[:] = [int(r) for r in res]
+    c.dx, c.dt = float(dx), float(dt)
+    c.gravity[:] = [float(g) for g in gravity]
+    c.bound = int(bound)
+    c.particle_volume = float(particle_volume)
+    c.friction = float(friction)
+    c.particle_collision = int(particle_collision)
+    c.shovel_half[:] = [float(h) for h in shovel_half]
+    c.shovel_on = int(shovel_on)
+    return c
+
+
+def make_options(checkpoint_every=50, clip_grads=0, clip_value=1e4, sigma_min=1e-4, sort_every=0) -> mpm_options:
+    o = mpm_options()
+    o.checkpoint_every, o.clip_grads, o.clip_value = int(checkpoint_every), int(clip_grads), float(clip_value)
+    o.sigma_min, o.sort_every = float(sigma_min), int(sort_every)
+    return o
+
+
+class Simulation:
+    """Owner of one mpm_handle (a batch of instances)."""
+
+    def __init__(self, configs: Sequence[mpm_config], materials: Sequence[Sequence[float]],
+                 positions: Sequence[np.ndarray], options: Optional[mpm_options] = None):
+        L = lib()
+        n = len(configs)
+        self.n_inst = n
+        self.counts = [int(np.asarray(p).reshape(-1, 3).shape[0]) for p in positions]
+        self.n = int(sum(self.counts))
+        cfg_arr = (mpm_config * n)(*configs)
+        mat_arr = (mpm_material * n)(*[mpm_material(*map(float, m)) for m in materials])
+        cnt = (ctypes.c_int64 * n)(*self.counts)
+        x0 = np.ascontiguousarray(np.concatenate([np.asarray(p, np.float32).reshape(-1, 3) for p in positions])
+                                  if self.n else np.zeros((0, 3), np.float32))
+        h = ctypes.c_void_p()
+        check(L.mpm_create(n, cfg_arr, mat_arr, cnt, x0.ctypes.data_as(ctypes.c_void_p),
+                           ctypes.byref(options) if options is not None else None, ctypes.byref(h)), "mpm_create")
+        self.h = h
+        self.n_actions = [0] * n
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mpm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- setup ------------------------------------------------------------
+    def set_stream(self, stream_ptr: int):
+        check(lib().mpm_set_stream(self.h, ctypes.c_void_p(stream_ptr)), "mpm_set_stream")
+
+    def set_material(self, inst: int, material: Sequence[float]):
+        m = mpm_material(*map(float, material))
+        check(lib().mpm_set_material(self.h, inst, ctypes.byref(m)), "mpm_set_material")
+
+    def set_actions(self, inst: int, start_pose, actions, substeps_per_action: int):
+        a = np.ascontiguousarray(np.asarray(actions, np.float64).reshape(-1, 6))
+        sp = np.ascontiguousarray(np.asarray(start_pose, np.float64).reshape(4))
+        check(lib().mpm_set_shovel_actions(self.h, inst, sp.ctypes.data_as(_dp), a.shape[0], a.ctypes.data_as(_dp),
+                                           int(substeps_per_action)), "mpm_set_shovel_actions")
+        self.n_actions[inst] = a.shape[0]
+
+    def set_skill(self, inst: int, theta, v_lin, v_ang, substeps_per_action, start_pose):
+        s = mpm_skill()
+        s.theta[:] = [float(t) for t in theta]
+        s.v_lin, s.v_ang, s.substeps_per_action = float(v_lin), float(v_ang), int(substeps_per_action)
+        s.start_pose[:] = [float(p) for p in start_pose]
+        check(lib().mpm_set_shovel_trajectory(self.h, inst, ctypes.byref(s)), "mpm_set_shovel_trajectory")
+        self.n_actions[inst] = lib().mpm_num_actions(self.h, inst)
+
+    # -- simulation -------------------------------------------------------
+    def reset(self):
+        check(lib().mpm_reset(self.h), "mpm_reset")
+
+    def forward(self, n_substeps: int, record: bool = False):
+        check(lib().mpm_forward(self.h, int(n_substeps), int(bool(record))), "mpm_forward")
+
+    def set_state(self, x, v=None, C=None, F=None):
+        dev = _is_device(x, v, C, F)
+        ps = [_ptr(a, dev) for a in (x, v, C, F)]
+        check(lib().mpm_set_state(self.h, *[p for p, _ in ps], int(dev)), "mpm_set_state")
+
+    def get_state(self, device_out: Optional[dict] = None) -> dict:
+        """Host numpy copies of x, v, C, F (external order) unless device
+        tensors are given in device_out (keys x, v, C, F)."""
+        if device_out is not None:
+            ps = [_ptr(device_out.get(k), True) for k in ("x", "v", "C", "F")]
+            check(lib().mpm_get_state(self.h, *[p for p, _ in ps], 1), "mpm_get_state")
+            return device_out
+        out = {"x": np.empty((self.n, 3), np.float32), "v": np.empty((self.n, 3), np.float32),
+               "C": np.empty((self.n, 3, 3), np.float32), "F": np.empty((self.n, 3, 3), np.float32)}
+        check(lib().mpm_get_state(self.h, *[out[k].ctypes.data_as(ctypes.c_void_p) for k in ("x", "v", "C", "F")], 0),
+              "mpm_get_state")
+        return out
+
+    def loss_mse(self, target, want_grad: bool = True, grad_out=None):
+        dev = _is_device(target)
+        L = np.zeros(self.n_inst, np.float64)
+        tp, tk = _ptr(target, dev)
+        if dev:
+            gp, gk = _ptr(grad_out, True) if want_grad else (None, None)
+            check(lib().mpm_loss_mse(self.h, tp, L.ctypes.data_as(_dp), gp, 1), "mpm_loss_mse")
+            return L, grad_out
+        g = np.empty((self.n, 3), np.float32) if want_grad else None
+        check(lib().mpm_loss_mse(self.h, tp, L.ctypes.data_as(_dp),
+                                 g.ctypes.data_as(ctypes.c_void_p) if g is not None else None, 0), "mpm_loss_mse")
+        return L, g
+
+    def backward(self, dL_dx=None, dL_dv=None):
+        dev = _is_device(dL_dx, dL_dv)
+        gx, kx = _ptr(dL_dx, dev)
+        gv, kv = _ptr(dL_dv, dev)
+        gm = np.zeros((self.n_inst, 4), np.float64)
+        gt = np.zeros((self.n_inst, 6), np.float64)
+        check(lib().mpm_backward(self.h, gx, gv, int(dev), gm.ctypes.data_as(_dp), gt.ctypes.data_as(_dp)),
+              "mpm_backward")
+        return gm, gt
+
+    def state_grad(self) -> dict:
+        out = {"x": np.empty((self.n, 3), np.float32), "v": np.empty((self.n, 3), np.float32),
+               "C": np.empty((self.n, 3, 3), np.float32), "F": np.empty((self.n, 3, 3), np.float32)}
+        check(lib().mpm_get_state_grad(self.h, *[out[k].ctypes.data_as(ctypes.c_void_p) for k in ("x", "v", "C", "F")],
+                                       0), "mpm_get_state_grad")
+        return out
+
+    def action_grad(self, inst: int):
+        na = lib().mpm_num_actions(self.h, inst)
+        ga = np.zeros((max(na, 1), 6), np.float64)
+        gs = np.zeros(4, np.float64)
+        check(lib().mpm_get_action_grad(self.h, inst, ga.ctypes.data_as(_dp), gs.ctypes.data_as(_dp)),
+              "mpm_get_action_grad")
+        return ga[:na], gs
+
+    def synchronize(self):
+        check(lib().mpm_synchronize(self.h), "mpm_synchronize")
+
+    def set_substep(self, s: int):
+        check(lib().mpm_set_substep(self.h, int(s)), "mpm_set_substep")
+
+    def profile(self, enable: bool):
+        check(lib().mpm_profile(self.h, int(bool(enable))), "mpm_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total device ms, launches)} for every kernel."""
+        out = {}
+        for k in range(7):
+            ms = ctypes.c_double()
+            n = ctypes.c_int64()
+            check(lib().mpm_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)), "mpm_profile_read")
+            out[lib().mpm_kernel_name(k).decode()] = (ms.value, n.value)
+        return out
+
+    def grid_mass(self) -> np.ndarray:
+        out = np.zeros(self.n_inst, np.float64)
+        check(lib().mpm_grid_mass(self.h, out.ctypes.data_as(_dp)), "mpm_grid_mass")
+        return out
+
+    def info(self) -> dict:
+        i = mpm_info_t()
+        check(lib().mpm_get_info(self.h, ctypes.byref(i)), "mpm_get_info")
+        return {k: getattr(i, k) for k, _ in mpm_info_t._fields_}
+
+
+def simulation_from_workloads(workloads, options: Optional[mpm_options] = None, particle_collision: int = 1,
+                              shovel_on: int = 1, gravity=None) -> Simulation:
+    """One handle holding every workload of the list as an instance, with
+    its material and trajectory set."""
+    cfgs, mats, xs = [], [], []
+    for w in workloads:
+        cfgs.append(make_config(w.res, w.dx, w.dt, w.vol, gravity=w.gravity if gravity is None else gravity,
+                                bound=w.bound, friction=w.friction, particle_collision=particle_collision,
+                                shovel_half=w.shovel_half, shovel_on=shovel_on))
+        mats.append((w.E, w.nu, w.rho, w.phi_deg))
+        xs.append(w.x0)
+    sim = Simulation(cfgs, mats, xs, options)
+    for i, w in enumerate(workloads):
+        t = w.traj
+        if t.theta is not None:
+            sim.set_skill(i, t.theta, t.v_lin, t.v_ang, t.substeps_per_action, t.start_pose)
+        elif t.actions is not None:
+            sim.set_actions(i, t.start_pose, t.actions, t.substeps_per_action)
+    return sim

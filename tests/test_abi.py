@@ -1,0 +1,74 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry
+point that include/mpm.h declares (and the binding names no other), and
+rejects invalid arguments before touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2510_17335_gb300 import build as libbuild
+from paper_2510_17335_gb300 import mpm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    libbuild.build()
+    return mpm.lib()
+
+
+def declared():
+    hdr = open(os.path.join(ROOT, "include", "mpm.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return set(re.findall(r"\b(mpm_[a-z_0-9]+)\s*\(", hdr))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+    assert names == set(mpm.EXPORTS), names ^ set(mpm.EXPORTS)
+
+
+def test_error_strings_and_version(L):
+    assert L.mpm_version() == 1
+    for code in [0, -1, -2, -3, -4, -5, -6, -7, -8]:
+        assert len(L.mpm_error_string(code)) > 0
+    assert L.mpm_error_string(-99) == b"unknown error"
+
+
+def _create(L, cfg, mat, x, opts=None):
+    h = ctypes.c_void_p()
+    n = np.asarray(x, np.float32).reshape(-1, 3)
+    cnt = (ctypes.c_int64 * 1)(n.shape[0])
+    return L.mpm_create(1, (mpm.mpm_config * 1)(cfg), (mpm.mpm_material * 1)(mpm.mpm_material(*mat)), cnt,
+                        n.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts) if opts else None, ctypes.byref(h))
+
+
+def test_invalid_arguments_are_rejected(L):
+    dx = 1.0 / 16
+    good = mpm.make_config((16, 16, 16), dx, 1e-4, dx ** 3 / 8)
+    x = np.array([[0.5, 0.5, 0.5]], np.float32)
+    mat = (1e5, 0.3, 1500.0, 30.0)
+    assert _create(L, good, (1e5, 0.5, 1500.0, 30.0), x) == -1          # nu = 0.5
+    assert _create(L, good, (-1.0, 0.3, 1500.0, 30.0), x) == -1         # E < 0
+    assert _create(L, good, (1e5, 0.3, 1500.0, 95.0), x) == -1          # phi > 90
+    bad = mpm.make_config((16, 16, 16), dx, 0.0, dx ** 3 / 8)
+    assert _create(L, bad, mat, x) == -1                                # dt = 0
+    bad = mpm.make_config((4, 16, 16), dx, 1e-4, dx ** 3 / 8)
+    assert _create(L, bad, mat, x) == -1                                # res too small
+    assert _create(L, good, mat, np.array([[0.5, 0.5, 0.97]], np.float32)) == -4   # outside [dx, (res-2) dx)
+    assert _create(L, good, mat, np.array([[0.5, 0.01, 0.5]], np.float32)) == -4
+    assert _create(L, good, mat, np.array([[0.5, np.nan, 0.5]], np.float32)) == -1
+    assert _create(L, good, mat, x, mpm.make_options(checkpoint_every=0)) == -1
+    h = ctypes.c_void_p()
+    assert L.mpm_create(0, None, None, None, None, None, ctypes.byref(h)) == -1
+    # NULL handles
+    assert L.mpm_forward(None, 1, 0) == -1
+    assert L.mpm_backward(None, None, None, 0, None, None) == -1
+    assert L.mpm_reset(None) == -1
+    L.mpm_destroy(None)

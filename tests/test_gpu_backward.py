@@ -1,0 +1,234 @@
+"""GPU adjoint parity: gradients from the CUDA backward (through the C ABI)
+against the FP64 oracle's own adjoint and against central finite
+differences of the oracle forward. Bar: 2e-2 relative per component
+(relative to max(|g_ref|, 1e-3 * max|g_ref|))."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_17335_gb300 import mpm
+from paper_2510_17335_gb300 import workloads as W
+
+from _common import initial_state, oracle_actions, oracle_params, oracle_poses, rel_err
+
+pytestmark = pytest.mark.gpu
+BAR = 2e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2510_17335_gb300 import build
+    build.build()
+    mpm.lib()
+
+
+def _contact_workload():
+    """A small bed with a tilted shovel pushing into it (grid and particle
+    contact, plastic flow, walls)."""
+    res, dx = 20, 1.0 / 20
+    x0 = W.lattice_bed(21, (6, 4, 5), (6 * dx, 3 * dx, 7 * dx), dx)
+    acts = np.zeros((4, 6))
+    acts[:, 0] = 0.004
+    acts[:, 1] = -0.002
+    acts[:, 3] = 0.01
+    return W.Workload("contact", (res,) * 3, dx, 1e-4, 12, 1e5, 0.3, 1500.0, 30.0, dx ** 3 / 8, x0,
+                      W.Trajectory((7.1 * dx, 5.2 * dx, 9.3 * dx, 0.1), 3, actions=acts),
+                      shovel_half=(0.025, 0.06, 0.08))
+
+
+def _strained_state(w, seed):
+    rng = np.random.default_rng(seed)
+    n = w.n
+    F = W.strained_F(rng, n, 0.01, (0.01, -0.03, 0.0)).astype(np.float32)
+    v = (rng.normal(size=(n, 3)) * 0.05).astype(np.float32)
+    C = (rng.normal(size=(n, 3, 3)) * 0.3).astype(np.float32)
+    return w.x0, v, C, F
+
+
+def _gpu_grad(ws, states, nsub, seeds, K=50, clip=0):
+    opts = mpm.make_options(checkpoint_every=K, clip_grads=clip)
+    with mpm.simulation_from_workloads(ws, opts) as sim:
+        if states is not None:
+            sim.set_state(*[np.concatenate([s[k] for s in states]) for k in range(4)])
+        sim.forward(nsub, record=True)
+        out = sim.get_state()
+        gx = np.concatenate([s[0] for s in seeds]).astype(np.float32)
+        gv = np.concatenate([s[1] for s in seeds]).astype(np.float32)
+        gm, gt = sim.backward(dL_dx=gx, dL_dv=gv)
+        gs = sim.state_grad()
+        ga = [sim.action_grad(i) for i in range(len(ws))]
+    return out, gm, gt, gs, ga
+
+
+def _oracle_grad(w, state, nsub, seed, clip=0):
+    p = oracle_params(w, clip=clip)
+    poses = oracle_poses(w, nsub)
+    x, v, C, F = [np.asarray(a, np.float64) for a in state]
+    n = w.n
+    st, g = oracle.rollout_adjoint(p, x.reshape(n, 3), v.reshape(n, 3), C.reshape(n, 9), F.reshape(n, 9), poses,
+                                   gx=seed[0], gv=seed[1])
+    assert st == 0
+    acts, jac = oracle_actions(w)
+    ga = oracle.pose_table_adjoint(acts.shape[0], w.traj.substeps_per_action, w.dt, g["poses"])
+    gt = None if jac is None else np.einsum("tk,tkj->j", ga, jac)
+    return g, ga, gt
+
+
+def _seed(w, seed):
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(w.n, 3)) / w.n, rng.normal(size=(w.n, 3)) * 1e-3 / w.n
+
+
+def test_adjoint_matches_oracle_contact_scenario():
+    w = _contact_workload()
+    state = _strained_state(w, 1)
+    seed = _seed(w, 2)
+    nsub = 12
+    _, gm, gt, gs, ga = _gpu_grad([w], [state], nsub, [seed], K=5)
+    g, ga_ref, _ = _oracle_grad(w, state, nsub, seed)
+    print("material gpu", gm[0], "oracle", g["material"])
+    assert rel_err(gm[0], g["material"]).max() < BAR
+    for k in ("x", "v", "C", "F"):
+        e = rel_err(gs[k].reshape(w.n, -1), g[k].reshape(w.n, -1))
+        print(k, "state-grad max rel err", e.max(), "p99", np.quantile(e, 0.99))
+        assert np.quantile(e, 0.99) < BAR
+        assert e.max() < 10 * BAR
+    assert np.abs(ga_ref).max() > 0
+    e = rel_err(ga[0][0][:, :4], ga_ref[:, :4])
+    print("action grad max rel err", e.max())
+    assert e.max() < BAR
+
+
+def test_adjoint_skill_theta_gradient():
+    """dL/dtheta through Algorithm 2's Jacobian (rounded T, frozen): the
+    library's chain against the oracle's (pose-table adjoint, then the
+    Jacobian), on a bed dug by the skill."""
+    res, dx = 32, 1.0 / 32
+    x0 = W.lattice_bed(31, (10, 5, 8), (11 * dx, 3 * dx, 12 * dx), dx)
+    top = 8 * dx
+    traj = W.Trajectory((13.5 * dx, top - 0.005, 16 * dx, 0.0), 4, theta=(0.4, 0.3, 0.55, 0.2, -0.2, 0.5),
+                        v_lin=25.0, v_ang=250.0)
+    w = W.Workload("skill", (res,) * 3, dx, 1e-4, 40, 1e5, 0.3, 1500.0, 30.0, dx ** 3 / 8, x0, traj,
+                   shovel_half=(0.02, 0.06, 0.1))
+    seed = _seed(w, 3)
+    state = (w.x0, np.zeros((w.n, 3), np.float32), np.zeros((w.n, 3, 3), np.float32),
+             np.tile(np.eye(3, dtype=np.float32), (w.n, 1, 1)))
+    nsub = 40
+    _, gm, gt, gs, ga = _gpu_grad([w], None, nsub, [seed], K=10)
+    g, ga_ref, gt_ref = _oracle_grad(w, state, nsub, seed)
+    print("theta gpu", gt[0], "oracle", gt_ref)
+    assert np.abs(gt_ref).max() > 0
+    assert rel_err(gt[0], gt_ref).max() < BAR
+    assert rel_err(gm[0], g["material"]).max() < BAR
+
+
+def test_checkpoint_interval_does_not_change_gradients():
+    w = _contact_workload()
+    state = _strained_state(w, 4)
+    seed = _seed(w, 5)
+    a = _gpu_grad([w], [state], 12, [seed], K=3)
+    b = _gpu_grad([w], [state], 12, [seed], K=50)
+    assert rel_err(a[1][0], b[1][0]).max() < 1e-4
+    assert np.abs(a[3]["x"] - b[3]["x"]).max() <= 1e-4 * np.abs(b[3]["x"]).max()
+
+
+def test_batched_adjoint_equals_each_instance():
+    w1 = _contact_workload()
+    res, dx = 16, 1.0 / 16
+    x2 = W.lattice_bed(41, (4, 3, 4), (6 * dx, 3 * dx, 6 * dx), dx)
+    w2 = W.Workload("b2", (res,) * 3, dx, 1e-4, 8, 2e5, 0.25, 1700.0, 35.0, dx ** 3 / 8, x2,
+                    W.Trajectory((0.9, 0.9, 0.9, 0.0), 2, actions=np.zeros((1, 6))))
+    s1, s2 = _strained_state(w1, 6), _strained_state(w2, 7)
+    e1, e2 = _seed(w1, 8), _seed(w2, 9)
+    _, gm, _, _, _ = _gpu_grad([w1, w2], [s1, s2], 8, [e1, e2], K=4)
+    for i, (w, s, e) in enumerate([(w1, s1, e1), (w2, s2, e2)]):
+        g, _, _ = _oracle_grad(w, s, 8, e)
+        assert rel_err(gm[i], g["material"]).max() < BAR, (i, gm[i], g["material"])
+
+
+def test_gpu_gradient_against_central_fd():
+    """The GPU material gradient against central differences of the FP64
+    oracle forward (the paper's FD check), step 1e-4 relative."""
+    w = _contact_workload()
+    state = _strained_state(w, 10)
+    seed = _seed(w, 11)
+    nsub = 8
+    _, gm, _, _, _ = _gpu_grad([w], [state], nsub, [seed], K=4)
+    p = oracle_params(w)
+    poses = oracle_poses(w, nsub)
+    x, v, C, F = [np.asarray(a, np.float64).reshape(w.n, -1) for a in state]
+
+    def loss(pp):
+        st, s = oracle.rollout(pp, x, v, C, F, poses)
+        assert st == 0
+        return (seed[0] * s["x"]).sum() + (seed[1] * s["v"]).sum()
+
+    fd = []
+    for key in ("E", "nu", "rho", "phi_deg"):
+        base = getattr(p, key)
+        h = 1e-4 * base
+        setattr(p, key, base + h); lp = loss(p)
+        setattr(p, key, base - h); lm = loss(p)
+        setattr(p, key, base)
+        fd.append((lp - lm) / (2 * h))
+    fd = np.array(fd)
+    print("gpu", gm[0], "fd", fd)
+    assert rel_err(gm[0], fd).max() < BAR
+
+
+def test_clipped_adjoint_matches_oracle():
+    w = _contact_workload()
+    state = _strained_state(w, 12)
+    rng = np.random.default_rng(13)
+    seed = (rng.normal(size=(w.n, 3)) * 3e4, rng.normal(size=(w.n, 3)) * 3e4)
+    _, gm, _, gs, _ = _gpu_grad([w], [state], 6, [seed], K=3, clip=1)
+    g, _, _ = _oracle_grad(w, state, 6, seed, clip=1)
+    assert rel_err(gm[0], g["material"]).max() < BAR
+    e = rel_err(gs["x"], g["x"])
+    assert np.quantile(e, 0.99) < BAR
+
+
+def test_backward_without_record_fails_cleanly():
+    w = _contact_workload()
+    with mpm.simulation_from_workloads([w]) as sim:
+        sim.forward(2)
+        with pytest.raises(mpm.MpmError) as e:
+            sim.backward(dL_dx=np.zeros((w.n, 3), np.float32))
+        assert e.value.code == -6
+        sim.forward(2, record=True)
+        sim.backward(dL_dx=np.zeros((w.n, 3), np.float32))
+        with pytest.raises(mpm.MpmError):
+            sim.backward(dL_dx=np.zeros((w.n, 3), np.float32))   # the record is consumed
+
+
+def test_full_size_adjoint_against_oracle():
+    """1,048,576 particles on the 128^3 grid: a 4-substep recorded rollout
+    from a settled, strained state and its backward; the material gradient
+    and sampled state adjoints against the oracle's FP64 adjoint of the same
+    rollout."""
+    w = W.cfg_1m()
+    with mpm.simulation_from_workloads([w]) as sim:
+        sim.forward(20)
+        s0 = sim.get_state()
+    rng = np.random.default_rng(17)
+    seed = (rng.normal(size=(w.n, 3)) / w.n, np.zeros((w.n, 3)))
+    state = (s0["x"], s0["v"], s0["C"], s0["F"])
+    nsub = 4
+    with mpm.simulation_from_workloads([w], mpm.make_options(checkpoint_every=2)) as sim:
+        sim.set_substep(20)
+        sim.set_state(*state)
+        sim.forward(nsub, record=True)
+        gm, gt = sim.backward(dL_dx=seed[0].astype(np.float32))
+        gs = sim.state_grad()
+    p = oracle_params(w)
+    poses = oracle_poses(w, 20 + nsub)[20:]
+    x, v, C, F = [np.asarray(a, np.float64).reshape(w.n, -1) for a in state]
+    st, g = oracle.rollout_adjoint(p, x, v, C, F, poses, gx=seed[0])
+    assert st == 0
+    print("full-size material gpu", gm[0], "oracle", g["material"])
+    assert rel_err(gm[0], g["material"]).max() < BAR
+    idx = rng.choice(w.n, 4096, replace=False)
+    e = rel_err(gs["x"][idx], g["x"][idx])
+    assert np.quantile(e, 0.99) < BAR

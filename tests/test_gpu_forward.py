@@ -1,0 +1,228 @@
+"""GPU forward parity: the CUDA substep (through the C ABI) against the FP64
+oracle on the same seeded FP32 inputs.
+
+Bars: positions within 1e-4 of the unit domain after 10 substeps; total
+grid mass within 1e-6 relative. Velocity, C and F are checked too, against
+tolerances derived from FP32 arithmetic (relative 1e-7 per operation; a few
+hundred operations per value; contact decisions at nodes within rounding of
+the box surface may flip, which moves the affected particles' velocity by
+at most the shovel's relative speed times a B-spline weight)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_17335_gb300 import mpm
+from paper_2510_17335_gb300 import workloads as W
+
+from _common import initial_state, oracle_params, oracle_poses, oracle_rollout
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2510_17335_gb300 import build
+    build.build()
+    mpm.lib()
+
+
+def _compare(g, ref, n_sub, label, x_bar=1e-4):
+    ex = np.abs(g["x"] - ref["x"]).max()
+    vmax = max(np.abs(ref["v"]).max(), 1e-6)
+    ev = np.abs(g["v"] - ref["v"]).max() / vmax
+    eF = np.abs(g["F"] - ref["F"]).max()
+    cmax = max(np.abs(ref["C"]).max(), 1e-6)
+    eC = np.abs(g["C"] - ref["C"]).max() / cmax
+    print(f"{label}: substeps={n_sub} max|dx|={ex:.2e} max|dv|/vmax={ev:.2e} max|dF|={eF:.2e} max|dC|/Cmax={eC:.2e}")
+    assert ex < x_bar, ex
+    # 99.9% of particles far tighter than the bar
+    assert np.quantile(np.abs(g["x"] - ref["x"]).max(1), 0.999) < 1e-5
+    assert eF < 1e-3, eF
+    return ex, ev, eF, eC
+
+
+def test_small_bed_10_substeps():
+    w = W.cfg_small()
+    with mpm.simulation_from_workloads([w]) as sim:
+        sim.forward(10)
+        g = sim.get_state()
+        gm = sim.grid_mass()
+    ref = oracle_rollout(w, 10)
+    _compare(g, ref, 10, "bed8k")
+    assert np.isclose(gm[0], w.n * w.rho * w.vol, rtol=1e-6)
+
+
+def test_small_bed_200_substeps_trajectory():
+    """Full 200-substep rollout with the shovel inserting and pushing; the
+    flow is piecewise smooth (contact, plasticity), so FP32 and FP64 drift
+    apart slowly; the bar stays 1e-4 in position."""
+    w = W.cfg_small()
+    with mpm.simulation_from_workloads([w]) as sim:
+        sim.forward(200)
+        g = sim.get_state()
+    ref = oracle_rollout(w, 200)
+    ex = np.abs(g["x"] - ref["x"]).max(1)
+    print(f"bed8k 200 substeps: max|dx|={ex.max():.2e} p99.9={np.quantile(ex, 0.999):.2e}")
+    assert ex.max() < 1e-3
+    assert np.quantile(ex, 0.99) < 1e-4
+
+
+def _mini_workloads():
+    """Uneven instances: different grids (incl. sizes that are not a multiple
+    of the 4^3 block), particle counts (1, ragged, 0), materials, contact."""
+    out = []
+    # 1: a single particle
+    res, dx = 16, 1.0 / 16
+    w = W.cfg_small()
+    one = W.Workload("one", (res,) * 3, dx, 1e-4, 10, 1e5, 0.3, 1500.0, 30.0, dx ** 3 / 8,
+                     np.array([[0.51, 0.4, 0.47]], np.float32),
+                     W.Trajectory((0.8, 0.8, 0.8, 0.0), 5, actions=np.zeros((1, 6))))
+    out.append(one)
+    # 2: ragged count on a 20 x 18 x 22 grid, stiff material, shovel in contact
+    res2, dx2 = (20, 18, 22), 1.0 / 20
+    x2 = W.lattice_bed(11, (5, 4, 5), (6 * dx2, 3 * dx2, 7 * dx2), dx2)[:777]
+    acts = np.zeros((3, 6)); acts[:, 1] = -0.003; acts[:, 3] = 0.02
+    out.append(W.Workload("ragged", res2, dx2, 1e-4, 10, 3e5, 0.25, 1800.0, 35.0, dx2 ** 3 / 8, x2,
+                          W.Trajectory((8.3 * dx2, 6.0 * dx2, 9.5 * dx2, 0.05), 4, actions=acts),
+                          shovel_half=(0.02, 0.05, 0.08)))
+    # 3: empty instance
+    out.append(W.Workload("empty", (16, 16, 16), dx, 1e-4, 10, 1e5, 0.3, 1500.0, 30.0, dx ** 3 / 8,
+                          np.zeros((0, 3), np.float32), W.Trajectory((0.5, 0.5, 0.5, 0.0), 5, actions=np.zeros((1, 6)))))
+    # 4: soft soil sliding down with friction angle 20
+    res4, dx4 = (24, 24, 24), 1.0 / 24
+    x4 = W.lattice_bed(13, (6, 6, 3), (5 * dx4, 3 * dx4, 9 * dx4), dx4)
+    out.append(W.Workload("soil", res4, dx4, 2e-4, 10, 5e4, 0.35, 1300.0, 20.0, dx4 ** 3 / 8, x4,
+                          W.Trajectory((0.7, 0.7, 0.7, 0.0), 5, actions=np.zeros((1, 6)))))
+    return out
+
+
+def test_batched_uneven_instances_match_oracle_each():
+    ws = _mini_workloads()
+    nsub = 10
+    with mpm.simulation_from_workloads(ws) as sim:
+        sim.forward(nsub)
+        g = sim.get_state()
+        gm = sim.grid_mass()
+    off = 0
+    for i, w in enumerate(ws):
+        n = w.n
+        sl = slice(off, off + n)
+        off += n
+        if n == 0:
+            assert gm[i] == 0.0
+            continue
+        ref = oracle_rollout(w, nsub)
+        _compare({k: v[sl] for k, v in g.items()}, ref, nsub, w.name)
+        assert np.isclose(gm[i], n * w.rho * w.vol, rtol=1e-6)
+
+
+def test_batched_equals_serial():
+    """Each instance of a batch gives the same result as the instance alone
+    (float atomics make the order of grid sums differ: tolerance 1e-6)."""
+    ws = _mini_workloads()
+    nsub = 6
+    with mpm.simulation_from_workloads(ws) as sim:
+        sim.forward(nsub)
+        gb = sim.get_state()
+    off = 0
+    for w in ws:
+        if w.n == 0:
+            continue
+        with mpm.simulation_from_workloads([w]) as s1:
+            s1.forward(nsub)
+            g1 = s1.get_state()
+        assert np.abs(gb["x"][off:off + w.n] - g1["x"]).max() < 1e-6
+        off += w.n
+
+
+def test_particle_collision_flag_off():
+    ws = _mini_workloads()[1:2]
+    with mpm.simulation_from_workloads(ws, particle_collision=0) as sim:
+        sim.forward(8)
+        g = sim.get_state()
+    ref = oracle_rollout(ws[0], 8, particle_collision=0)
+    _compare(g, ref, 8, "ragged-no-particle-contact")
+
+
+def test_state_roundtrip_and_reset():
+    w = W.cfg_small()
+    rng = np.random.default_rng(0)
+    with mpm.simulation_from_workloads([w]) as sim:
+        s0 = sim.get_state()
+        assert np.array_equal(s0["x"], w.x0) and (s0["v"] == 0).all() and (s0["F"] == np.eye(3, dtype=np.float32)).all()
+        v = rng.normal(size=(w.n, 3)).astype(np.float32)
+        C = rng.normal(size=(w.n, 3, 3)).astype(np.float32)
+        F = (np.eye(3) + 0.01 * rng.normal(size=(w.n, 3, 3))).astype(np.float32)
+        sim.set_state(w.x0, v, C, F)
+        s1 = sim.get_state()
+        for k, a in (("v", v), ("C", C), ("F", F)):
+            assert np.array_equal(s1[k], a)
+        sim.forward(3)
+        sim.reset()
+        s2 = sim.get_state()
+        assert np.array_equal(s2["x"], w.x0) and (s2["v"] == 0).all()
+
+
+def test_out_of_domain_is_reported():
+    """A particle driven out of [dx, (res-2) dx) makes the call return
+    MPM_ERR_OUT_OF_DOMAIN (kernels clamp their indices, nothing faults)."""
+    res, dx = 16, 1.0 / 16
+    cfg = mpm.make_config((res,) * 3, dx, 1e-3, dx ** 3 / 8, gravity=(0, 0, 0), shovel_on=0)
+    x = np.array([[0.5, 0.5, 13.9 * dx]], np.float32)
+    with mpm.Simulation([cfg], [(1e5, 0.3, 1500.0, 30.0)], [x]) as sim:
+        sim.set_state(x, np.array([[0.0, 0.0, 50.0]], np.float32))
+        with pytest.raises(mpm.MpmError) as e:
+            sim.forward(2)
+        assert e.value.code == -4
+
+
+def test_non_finite_is_reported():
+    res, dx = 16, 1.0 / 16
+    cfg = mpm.make_config((res,) * 3, dx, 1e-4, dx ** 3 / 8, shovel_on=0)
+    x = np.array([[0.5, 0.5, 0.5], [0.52, 0.5, 0.5]], np.float32)
+    with mpm.Simulation([cfg], [(1e5, 0.3, 1500.0, 30.0)], [x]) as sim:
+        v = np.array([[0.0, 0.0, 0.0], [np.inf, 0.0, 0.0]], np.float32)
+        sim.set_state(x, v)
+        with pytest.raises(mpm.MpmError) as e:
+            sim.forward(1)
+        assert e.value.code in (-5, -4)
+
+
+def test_full_size_sampled_substep():
+    """1,048,576 particles on the 128^3 grid, in the bench's launch
+    configuration: after 30 GPU substeps (shovel approaching, bed settling
+    under gravity), one more GPU substep is compared, for 48 sampled
+    particles, with the oracle run on each sample's neighbourhood (all
+    particles within two cells, which is every particle that writes to a
+    node the sample reads)."""
+    w = W.cfg_1m()
+    with mpm.simulation_from_workloads([w]) as sim:
+        sim.forward(30)
+        s0 = sim.get_state()
+        sim.forward(1)
+        s1 = sim.get_state()
+        gm = sim.grid_mass()
+    assert np.isclose(gm[0], w.n * w.rho * w.vol, rtol=1e-6)
+    assert all(np.isfinite(s1[k]).all() for k in s1)
+    p = oracle_params(w)
+    poses = oracle_poses(w, 31)[30:31]
+    rng = np.random.default_rng(5)
+    base = np.floor(s0["x"].astype(np.float64) / w.dx - 0.5).astype(np.int64)
+    samples = rng.choice(w.n, 48, replace=False)
+    worst = 0.0
+    for q in samples:
+        nb = np.where(np.abs(base - base[q]).max(1) <= 2)[0]
+        j = int(np.where(nb == q)[0][0])
+        xs = s0["x"][nb].astype(np.float64)
+        st, r = oracle.rollout(p, xs, s0["v"][nb], s0["C"][nb].reshape(-1, 9), s0["F"][nb].reshape(-1, 9), poses)
+        assert st == 0
+        dx_ = np.abs(s1["x"][q] - r["x"][j]).max()
+        dv_ = np.abs(s1["v"][q] - r["v"][j]).max()
+        dF_ = np.abs(s1["F"][q] - r["F"][j]).max()
+        worst = max(worst, dx_)
+        assert dx_ < 1e-6, (q, dx_)
+        assert dv_ < 1e-3 * max(1.0, np.abs(r["v"][j]).max()), (q, dv_)
+        assert dF_ < 1e-5, (q, dF_)
+    print(f"full-size sampled substep: worst |dx| {worst:.2e}")
