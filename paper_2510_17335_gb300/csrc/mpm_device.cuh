@@ -22,27 +22,59 @@ template <> __device__ __forceinline__ double dlog<double>(double x) { return lo
 template <typename T> __device__ __forceinline__ T dexp(T x);
 template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
 template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
+template <typename T> __device__ __forceinline__ T dlog1p(T x);
+template <> __device__ __forceinline__ float dlog1p<float>(float x) { return log1pf(x); }
+template <> __device__ __forceinline__ double dlog1p<double>(double x) { return log1p(x); }
+template <typename T> __device__ __forceinline__ T dfma(T a, T b, T c);
+template <> __device__ __forceinline__ float dfma<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <> __device__ __forceinline__ double dfma<double>(double a, double b, double c) { return fma(a, b, c); }
 template <typename T> __device__ __forceinline__ T dexpm1(T x);
 template <> __device__ __forceinline__ float dexpm1<float>(float x) { return expm1f(x); }
 template <> __device__ __forceinline__ double dexpm1<double>(double x) { return expm1(x); }
 
-// Jacobi rotation threshold: skip when gpq^2 <= tol * gpp * gqq.
-template <typename T> __device__ __forceinline__ T jacobi_tol();
-template <> __device__ __forceinline__ float jacobi_tol<float>() { return 1e-14f; }
-template <> __device__ __forceinline__ double jacobi_tol<double>() { return 1e-30; }
+// Jacobi rotations are skipped only for an (almost) exactly zero off-diagonal:
+// H's entries are small, so any threshold tied to 1 would cap their accuracy.
+template <typename T> __device__ __forceinline__ T jacobi_tiny();
+template <> __device__ __forceinline__ float jacobi_tiny<float>() { return 1e-35f; }
+template <> __device__ __forceinline__ double jacobi_tiny<double>() { return 1e-300; }
 template <typename T> struct Sweeps;
 template <> struct Sweeps<float> { static constexpr int n = 4; };
 template <> struct Sweeps<double> { static constexpr int n = 10; };
 
 // ---------------------------------------------------------------------------
-// 3x3 SVD: cyclic Jacobi eigen-decomposition of G = F^T F (gives V and
-// sigma^2), then U from the columns of F V. U and V are proper rotations; the
-// smallest singular value carries the sign of det F.
+// 3x3 SVD: cyclic Jacobi eigen-decomposition of H = F^T F - I (gives V and
+// sigma^2 - 1), then U from the columns of F V. U and V are proper rotations;
+// the smallest singular value carries the sign of det F.
+//
+// H is formed with error-free products and sums (fma / TwoSum), so that its
+// eigenvalues keep full relative accuracy when F is close to a rotation: the
+// log strains 0.5 log1p(sigma^2 - 1) of a nearly unstrained particle are then
+// exact to a few ulps of themselves instead of to a few ulps of 1, which is
+// what the apex and yield decisions of the return mapping need in FP32.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
+    s = a + b;
+    const T bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// sum_k x_k y_k - shift, compensated
+template <typename T>
+__device__ __forceinline__ T dot3_minus(T x0, T y0, T x1, T y1, T x2, T y2, T shift) {
+    const T p0 = x0 * y0, p1 = x1 * y1, p2 = x2 * y2;
+    const T e0 = dfma<T>(x0, y0, -p0), e1 = dfma<T>(x1, y1, -p1), e2 = dfma<T>(x2, y2, -p2);
+    T s, c1, c2, c3;
+    two_sum<T>(p0, p1, s, c1);
+    two_sum<T>(s, p2, s, c2);
+    two_sum<T>(s, -shift, s, c3);
+    return s + (((c1 + c2) + c3) + ((e0 + e1) + e2));
+}
+
 template <typename T, int p, int q, int r>
 __device__ __forceinline__ void jacobi_rotate(T (&G)[3][3], T (&V)[3][3]) {
     const T gpq = G[p][q], gpp = G[p][p], gqq = G[q][q];
-    if (gpq * gpq <= jacobi_tol<T>() * gpp * gqq) return;
+    if (!(fabs(gpq) > jacobi_tiny<T>())) return;
     const T zeta = (gqq - gpp) / (T(2) * gpq);
     T t;
     if (fabs(zeta) > T(1e15))
@@ -64,14 +96,18 @@ __device__ __forceinline__ void jacobi_rotate(T (&G)[3][3], T (&V)[3][3]) {
     }
 }
 
+// h[k] = sigma_k^2 - 1 to full relative accuracy
 template <typename T>
-__device__ __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3], T (&V)[3][3]) {
+__device__ __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3], T (&V)[3][3], T (&h)[3]) {
     T G[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            G[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+            if (j >= i)
+                G[i][j] = dot3_minus<T>(F[0][i], F[0][j], F[1][i], F[1][j], F[2][i], F[2][j], i == j ? T(1) : T(0));
+            else
+                G[i][j] = G[j][i];
             V[i][j] = (i == j) ? T(1) : T(0);
         }
 #pragma unroll
@@ -112,6 +148,7 @@ __device__ __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3]
 #pragma unroll
             for (int k = 0; k < 3; k++) U[r][k] = (r == k) ? T(1) : T(0);
         s[0] = s[1] = s[2] = T(0);
+        h[0] = h[1] = h[2] = T(-1);
         return;
     }
     const T inv_si = T(1) / si;
@@ -159,6 +196,9 @@ __device__ __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3]
     s[i] = si;
     s[j] = sj;
     s[m] = sm;
+    h[0] = l0;
+    h[1] = l1;
+    h[2] = l2;
 }
 
 // ---------------------------------------------------------------------------
@@ -168,6 +208,7 @@ __device__ __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3]
 template <typename T>
 struct Spectral {
     T U[3][3], V[3][3], s[3];
+    T h[3];               // s^2 - 1, accurate for small strains
     T eps[3], deps[3];    // ln max(s, s_min) and its derivative in s
     T ehat[3], nh, tr, kappa;
     T shat[3], e[3], t[3];
@@ -180,7 +221,8 @@ __device__ __forceinline__ void return_map(Spectral<T>& S, T mu, T lam, T beta, 
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         const bool ok = S.s[k] > smin;
-        S.eps[k] = dlog<T>(ok ? S.s[k] : smin);
+        // ln s = 0.5 log1p(s^2 - 1), exact for s near 1
+        S.eps[k] = ok ? T(0.5) * dlog1p<T>(S.h[k]) : dlog<T>(smin);
         S.deps[k] = ok ? T(1) / S.s[k] : T(0);
         S.tr += S.eps[k];
     }
@@ -220,7 +262,7 @@ __device__ __forceinline__ void return_map(Spectral<T>& S, T mu, T lam, T beta, 
 template <typename T>
 __device__ __forceinline__ void constitutive_spectral(const T (&Ft)[3][3], T mu, T lam, T beta, T smin,
                                                       Spectral<T>& S) {
-    svd3<T>(Ft, S.U, S.s, S.V);
+    svd3<T>(Ft, S.U, S.s, S.V, S.h);
     return_map<T>(S, mu, lam, beta, smin);
 }
 

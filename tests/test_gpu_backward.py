@@ -150,7 +150,12 @@ def test_batched_adjoint_equals_each_instance():
 
 def test_gpu_gradient_against_central_fd():
     """The GPU material gradient against central differences of the FP64
-    oracle forward (the paper's FD check), step 1e-4 relative."""
+    oracle forward. The model is piecewise smooth: most particles of this
+    scenario sit on the Drucker-Prager cone, and a relative step of 1e-4 in
+    phi moves the cone across some of them (the FD then averages two
+    branches). The step is 1e-6 relative, where the differences have
+    converged (a 1e-5 and a 1e-6 step must agree to 2e-2 before the GPU is
+    compared)."""
     w = _contact_workload()
     state = _strained_state(w, 10)
     seed = _seed(w, 11)
@@ -165,16 +170,20 @@ def test_gpu_gradient_against_central_fd():
         assert st == 0
         return (seed[0] * s["x"]).sum() + (seed[1] * s["v"]).sum()
 
-    fd = []
-    for key in ("E", "nu", "rho", "phi_deg"):
-        base = getattr(p, key)
-        h = 1e-4 * base
-        setattr(p, key, base + h); lp = loss(p)
-        setattr(p, key, base - h); lm = loss(p)
-        setattr(p, key, base)
-        fd.append((lp - lm) / (2 * h))
-    fd = np.array(fd)
-    print("gpu", gm[0], "fd", fd)
+    def fd_at(rel):
+        out = []
+        for key in ("E", "nu", "rho", "phi_deg"):
+            base = getattr(p, key)
+            h = rel * base
+            setattr(p, key, base + h); lp = loss(p)
+            setattr(p, key, base - h); lm = loss(p)
+            setattr(p, key, base)
+            out.append((lp - lm) / (2 * h))
+        return np.array(out)
+
+    fd, fd5 = fd_at(1e-6), fd_at(1e-5)
+    print("gpu", gm[0], "fd(1e-6)", fd, "fd(1e-5)", fd5)
+    assert rel_err(fd5, fd).max() < BAR
     assert rel_err(gm[0], fd).max() < BAR
 
 
@@ -204,31 +213,45 @@ def test_backward_without_record_fails_cleanly():
 
 
 def test_full_size_adjoint_against_oracle():
-    """1,048,576 particles on the 128^3 grid: a 4-substep recorded rollout
-    from a settled, strained state and its backward; the material gradient
-    and sampled state adjoints against the oracle's FP64 adjoint of the same
-    rollout."""
+    """1,048,576 particles on the 128^3 grid in the bench's state (the skill
+    at substep 600, shovel inserting): a 4-substep recorded rollout and its
+    backward under the MSE loss against a shifted target; the material and
+    skill gradients and sampled state adjoints against the oracle's FP64
+    adjoint of the same rollout from the same FP32 start state."""
     w = W.cfg_1m()
+    start = 600
     with mpm.simulation_from_workloads([w]) as sim:
-        sim.forward(20)
+        sim.forward(start)
         s0 = sim.get_state()
-    rng = np.random.default_rng(17)
-    seed = (rng.normal(size=(w.n, 3)) / w.n, np.zeros((w.n, 3)))
     state = (s0["x"], s0["v"], s0["C"], s0["F"])
     nsub = 4
+    target = (w.x0 + np.array([0.003, -0.002, 0.001], np.float32)).astype(np.float32)
     with mpm.simulation_from_workloads([w], mpm.make_options(checkpoint_every=2)) as sim:
-        sim.set_substep(20)
+        sim.set_substep(start)
         sim.set_state(*state)
         sim.forward(nsub, record=True)
-        gm, gt = sim.backward(dL_dx=seed[0].astype(np.float32))
+        L, gxs = sim.loss_mse(target)
+        gm, gt = sim.backward(dL_dx=gxs)
         gs = sim.state_grad()
+        xs = sim.get_state()["x"]
     p = oracle_params(w)
-    poses = oracle_poses(w, 20 + nsub)[20:]
+    poses = oracle_poses(w, start + nsub)[start:]
     x, v, C, F = [np.asarray(a, np.float64).reshape(w.n, -1) for a in state]
-    st, g = oracle.rollout_adjoint(p, x, v, C, F, poses, gx=seed[0])
+    st, r = oracle.rollout(p, x, v, C, F, poses)
     assert st == 0
+    Lr, gx = oracle.mse_loss(r["x"], target)
+    assert np.isclose(L[0], Lr, rtol=1e-5)
+    st, g = oracle.rollout_adjoint(p, x, v, C, F, poses, gx=gx)
+    assert st == 0
+    acts, jac = oracle_actions(w)
+    ga = oracle.pose_table_adjoint(acts.shape[0], w.traj.substeps_per_action, w.dt,
+                                   np.concatenate([np.zeros((start, 8)), g["poses"]]))
+    gt_ref = np.einsum("tk,tkj->j", ga, jac)
     print("full-size material gpu", gm[0], "oracle", g["material"])
+    print("full-size theta gpu", gt[0], "oracle", gt_ref)
     assert rel_err(gm[0], g["material"]).max() < BAR
+    assert rel_err(gt[0], gt_ref).max() < BAR
+    rng = np.random.default_rng(17)
     idx = rng.choice(w.n, 4096, replace=False)
     e = rel_err(gs["x"][idx], g["x"][idx])
     assert np.quantile(e, 0.99) < BAR
