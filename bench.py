@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--start", type=int, default=600, help="substep of the rollout start state")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, help="shared-memory tile scatter (1) or global atomics (0)")
+    ap.add_argument("--sort", type=int, default=0, help="sort particles by grid block every n substeps (0: never)")
     return ap.parse_args()
 
 
@@ -203,7 +205,7 @@ def run_ours(args):
     w = W.cfg_1m()
     N, S, K = w.n, args.substeps, args.checkpoint
     stream = torch.cuda.Stream()
-    opts = mpm.make_options(checkpoint_every=K)
+    opts = mpm.make_options(checkpoint_every=K, tile_scatter=args.tile, sort_every=args.sort)
     sim = mpm.simulation_from_workloads([w], opts)
     sim.set_stream(stream.cuda_stream)
     dev = torch.device("cuda", local)
@@ -351,6 +353,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "bed1m_grid128: 1,048,576 particles, 128^3 grid, skill-driven box shovel",
                    "substeps_per_step": S, "checkpoint_every": K, "start_substep": args.start,
+                   "tile_scatter": args.tile, "sort_every": args.sort,
                    "l2": "inputs larger than L2 (96 MB state + 4.9 GB segment buffers per step)",
                    "parallelism": f"replicas x{ws}"},
         "fwd_value": fwd_value, "fwd_ms_per_step": fms / args.steps,

@@ -90,6 +90,7 @@ typedef struct {
     double clip_value;        /* [1e4] */
     double sigma_min;         /* [1e-4] singular values are clamped here before the log */
     int sort_every;           /* [0] reorder particles by grid block every n substeps (0: never) */
+    int tile_scatter;         /* [0] sum the 27-node scatters in shared-memory tiles per CTA */
 } mpm_options;
 
 /* Digging skill (Sec. III-B): theta = (displace, rotate, insert_dist,
@@ -147,9 +148,11 @@ int mpm_set_state(mpm_handle* h, const float* x, const float* v, const float* C,
 int mpm_get_state(mpm_handle* h, float* x, float* v, float* C, float* F, int device_ptrs);
 
 /* Advance all instances by n_substeps (>= 0). record = 1 keeps what the
- * backward needs: one state checkpoint every checkpoint_every substeps (the
- * backward recomputes each segment). A recording forward continues an
- * existing record only if the previous call recorded too. */
+ * backward needs: one state checkpoint every checkpoint_every substeps, and
+ * every state and grid of the current segment (the backward reverses the
+ * last segment directly and recomputes the earlier ones from their
+ * checkpoints). A recording forward continues an existing record only if
+ * the previous call recorded too. */
 int mpm_forward(mpm_handle* h, int n_substeps, int record);
 
 /* L_i = (1/N_i) sum_p |x_p - xhat_p|^2 per instance (FP64 accumulation) and,
@@ -183,7 +186,7 @@ int mpm_set_substep(mpm_handle* h, int64_t substep);
 /* Kernel timing: enable != 0 records a CUDA event pair around every kernel
  * launch on the handle's stream (counters reset on every call). Kernel ids:
  * 0 k_p2g, 1 k_grid, 2 k_g2p, 3 k_g2p_bwd, 4 k_grid_bwd, 5 k_p2g_bwd,
- * 6 k_grid_clear. mpm_profile_read waits for the recorded events and gives
+ * 6 k_grid_clear, 7 k_slot_clear. mpm_profile_read waits for the recorded events and gives
  * the summed device time (ms) and the launch count of one kernel. */
 int mpm_profile(mpm_handle* h, int enable);
 int mpm_profile_read(mpm_handle* h, int kernel, double* total_ms, int64_t* launches);

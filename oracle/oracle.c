@@ -382,11 +382,14 @@ static int shovel_inside(const orc_params* p, const double q[3], const double po
     double d[3];
     for (int k = 0; k < 3; k++) d[k] = fabs(l[k]) - p->shovel_half[k];
     if (!(d[0] < 0 && d[1] < 0 && d[2] < 0)) return 0;
+    /* nearest face; at an edge or corner (face distances within 1e-7 m of
+     * each other) the face of the lowest axis index is taken */
     int a = 0;
     for (int k = 1; k < 3; k++)
-        if (d[k] > d[a]) a = k;
+        if (d[k] > d[a] + 1e-7) a = k;
     nloc[0] = nloc[1] = nloc[2] = 0;
-    nloc[a] = l[a] >= 0 ? 1.0 : -1.0;
+    /* a point within 1e-7 m of the mid-plane takes the + face */
+    nloc[a] = l[a] > -1e-7 ? 1.0 : -1.0;
     n[0] = cs * nloc[0] + sn * nloc[1];
     n[1] = -sn * nloc[0] + cs * nloc[1];
     n[2] = nloc[2];

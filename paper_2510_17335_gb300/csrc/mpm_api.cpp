@@ -153,13 +153,26 @@ struct mpm_handle {
     bool recording = false;
     int64_t rec_start = 0, rec_len = 0;
     std::vector<DevBuf<float>> ckpt;
-    DevBuf<float> d_seg_state;
-    DevBuf<float4> d_seg_acc, d_seg_vout, d_gacc;
-    DevBuf<unsigned char> d_seg_flags;
+    // segment slots: state k of the segment in seg_state[k] (k = 0..K), the
+    // grids of substep k in seg_acc/seg_vout/seg_flags[k] (k = 0..K-1)
+    std::vector<DevBuf<float>> seg_state;
+    std::vector<DevBuf<float4>> seg_acc, seg_vout;
+    std::vector<DevBuf<unsigned char>> seg_flags;
+    std::vector<char> seg_dirty;      // grid slot k holds accumulators/flags to clear
+    int64_t seg_valid = -1;           // segment whose states/grids the slots hold
+    int seg_valid_len = 0;
+    DevBuf<float4> d_gacc;
+    bool gacc_dirty = true;
     DevBuf<float> d_adj;
     DevBuf<double> d_gmat, d_gpose;
     bool have_grad = false;
-    bool seg_grids_clean = true;
+    int tile_scatter = 1;
+    // particle sort by grid block
+    DevBuf<float> d_state2, d_adj2;
+    DevBuf<int> d_ext2, d_key, d_rank, d_bcount, d_bscan, d_part, d_perm, d_ext_rec;
+    std::vector<DevBuf<int>> seg_perm;
+    std::vector<char> seg_sorted;
+    int64_t since_sort = 1LL << 40;
     Profiler prof;
 };
 
@@ -240,6 +253,7 @@ InstDev make_instdev(const mpm_handle* h, const Instance& I) {
     d.blk_off = I.blk_off;
     d.pbeg = I.pbeg;
     d.node_off = I.node_off;
+    d.ext_off = I.ext_off;
     d.dx = (float)I.cfg.dx;
     d.inv_dx = (float)(1.0 / I.cfg.dx);
     d.dt = (float)I.cfg.dt;
@@ -371,6 +385,7 @@ StepArgs base_args(mpm_handle* h) {
     a.status = h->d_status.p;
     a.fp64_count = h->d_fp64.p;
     a.clip = h->opt.clip_grads ? (float)h->opt.clip_value : 0.0f;
+    a.tile = h->tile_scatter;
     return a;
 }
 
@@ -422,6 +437,85 @@ int run_substep(mpm_handle* h, const StepArgs& a) {
     RK(run_kernel(h, KernelId::P2G, A));
     RK(run_kernel(h, KernelId::Grid, A));
     RK(run_kernel(h, KernelId::G2P, A));
+    return MPM_OK;
+}
+
+// make segment slot k usable: state k+1 (and 0) and grid k, zeroed when new
+int ensure_slot(mpm_handle* h, int k) {
+    const size_t state_floats = (size_t)h->ncap * kStateComps;
+    const size_t need = (size_t)k + 2;
+    if (h->seg_state.size() < need) h->seg_state.resize(need);
+    if (h->seg_acc.size() < need - 1) {
+        h->seg_acc.resize(need - 1);
+        h->seg_vout.resize(need - 1);
+        h->seg_flags.resize(need - 1);
+        h->seg_dirty.resize(need - 1, 0);
+    }
+    for (size_t i = 0; i < need; i++) RK(h->seg_state[i].ensure(state_floats, h->device_bytes));
+    if (h->seg_acc[k].p == nullptr) {
+        RK(h->seg_acc[k].ensure((size_t)h->n_nodes, h->device_bytes));
+        RK(h->seg_vout[k].ensure((size_t)h->n_nodes, h->device_bytes));
+        RK(h->seg_flags[k].ensure((size_t)h->n_blocks, h->device_bytes));
+        CK(cudaMemsetAsync(h->seg_acc[k].p, 0, (size_t)h->n_nodes * sizeof(float4), h->stream));
+        CK(cudaMemsetAsync(h->seg_flags[k].p, 0, (size_t)h->n_blocks, h->stream));
+        h->seg_dirty[k] = 0;
+    }
+    return MPM_OK;
+}
+
+// forward arguments for substep k of a segment (states k -> k+1, grid slot k, kept)
+StepArgs slot_args(mpm_handle* h, int k, int64_t substep) {
+    StepArgs a = base_args(h);
+    a.sin = h->seg_state[k].p;
+    a.sout = h->seg_state[k + 1].p;
+    a.acc = h->seg_acc[k].p;
+    a.vout = h->seg_vout[k].p;
+    a.flags = h->seg_flags[k].p;
+    a.keep_grid = 1;
+    a.substep = (int)substep;
+    return a;
+}
+
+// run one recorded substep into slot k (clearing the slot's old accumulators first)
+int run_slot_substep(mpm_handle* h, int k, int64_t substep) {
+    RK(ensure_slot(h, k));
+    StepArgs a = slot_args(h, k, substep);
+    if (h->seg_dirty[k]) {
+        AdjArgs C;
+        std::memset(&C, 0, sizeof C);
+        C.f = a;
+        RK(run_kernel(h, KernelId::SlotClear, C));
+    }
+    RK(run_substep(h, a));
+    h->seg_dirty[k] = 1;
+    return MPM_OK;
+}
+
+int copy_state(mpm_handle* h, float* dst, const float* src) {
+    if (dst == src) return MPM_OK;
+    CK(cudaMemcpyAsync(dst, src, (size_t)h->ncap * kStateComps * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    return MPM_OK;
+}
+
+// reorder every instance's particles by cell (d_state and the external
+// map in place); perm[new slot] = old slot
+int sort_particles(mpm_handle* h, int* perm) {
+    const size_t nc = (size_t)h->ncap;
+    RK(h->d_state2.ensure(nc * kStateComps, h->device_bytes));
+    RK(h->d_ext2.ensure(nc, h->device_bytes));
+    RK(h->d_key.ensure(nc, h->device_bytes));
+    RK(h->d_rank.ensure(nc, h->device_bytes));
+    const int n_keys = (int)h->n_nodes;   // one key per cell (cells and nodes share the blocked layout)
+    RK(h->d_bcount.ensure((size_t)n_keys, h->device_bytes));
+    RK(h->d_bscan.ensure((size_t)n_keys, h->device_bytes));
+    RK(h->d_part.ensure((size_t)(n_keys + 1023) / 1024, h->device_bytes));
+    CK(launch_sort(h->d_inst.p, h->d_chunk_inst.p, h->n_chunks, h->ncap, n_keys, h->d_state.p, h->d_state2.p,
+                   h->d_ext_of_slot.p, h->d_ext2.p, h->d_key.p, h->d_rank.p, h->d_bcount.p, h->d_bscan.p, h->d_part.p,
+                   perm, h->stream));
+    h->launches += kSortLaunches;
+    std::swap(h->d_state, h->d_state2);
+    std::swap(h->d_ext_of_slot, h->d_ext2);
+    h->since_sort = 0;
     return MPM_OK;
 }
 
@@ -495,7 +589,9 @@ int mpm_create(int n_inst, const mpm_config* cfgs, const mpm_material* mats, con
     h->opt.clip_value = 1e4;
     h->opt.sigma_min = 1e-4;
     h->opt.sort_every = 0;
+    h->opt.tile_scatter = 0;
     if (opts) h->opt = *opts;
+    h->tile_scatter = h->opt.tile_scatter ? 1 : 0;
     h->n_ext = n_ext;
     long long pbeg = 0, node = 0;
     int blk = 0, chunks = 0;
@@ -577,8 +673,15 @@ void mpm_destroy(mpm_handle* h) {
     h->d_acc.release(); h->d_vout.release(); h->d_flags.release(); h->d_status.release(); h->d_fp64.release();
     h->d_loss.release();
     for (auto& c : h->ckpt) c.release();
-    h->d_seg_state.release(); h->d_seg_acc.release(); h->d_seg_vout.release(); h->d_gacc.release();
-    h->d_seg_flags.release(); h->d_adj.release(); h->d_gmat.release(); h->d_gpose.release();
+    for (auto& b : h->seg_state) b.release();
+    for (auto& b : h->seg_acc) b.release();
+    for (auto& b : h->seg_vout) b.release();
+    for (auto& b : h->seg_flags) b.release();
+    h->d_gacc.release();
+    h->d_adj.release(); h->d_gmat.release(); h->d_gpose.release();
+    h->d_state2.release(); h->d_adj2.release(); h->d_ext2.release(); h->d_key.release(); h->d_rank.release();
+    h->d_bcount.release(); h->d_bscan.release(); h->d_part.release(); h->d_perm.release(); h->d_ext_rec.release();
+    for (auto& b : h->seg_perm) b.release();
     h->prof.release();
     if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -610,6 +713,7 @@ int mpm_set_material(mpm_handle* h, int inst, const mpm_material* mat) {
     RK(set_device(h));
     h->inst[inst].mat = *mat;
     h->recording = false;
+    h->seg_valid = -1;
     return upload_instances(h);
 }
 
@@ -635,6 +739,7 @@ int mpm_set_shovel_actions(mpm_handle* h, int inst, const double start_pose[4], 
     I.actions.assign(actions, actions + (size_t)n_actions * 6);
     I.jac.clear();
     h->recording = false;
+    h->seg_valid = -1;
     return upload_poses(h);
 }
 
@@ -670,6 +775,7 @@ int mpm_reset(mpm_handle* h) {
     CK(cudaStreamSynchronize(h->stream));
     h->substep = 0;
     h->recording = false;
+    h->seg_valid = -1;
     h->rec_len = 0;
     return MPM_OK;
 }
@@ -691,6 +797,7 @@ int mpm_set_state(mpm_handle* h, const float* x, const float* v, const float* C,
     CK(launch_state_from_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, dx, dv, dC, dF, h->d_state.p, h->stream));
     h->launches++;
     h->recording = false;
+    h->seg_valid = -1;
     h->rec_len = 0;
     if (!device_ptrs) CK(cudaStreamSynchronize(h->stream));
     return MPM_OK;
@@ -730,30 +837,79 @@ int mpm_forward(mpm_handle* h, int n_substeps, int record) {
         }
     } else {
         h->recording = false;
+    h->seg_valid = -1;
         h->rec_len = 0;
+        h->seg_valid = -1;
     }
     const size_t state_floats = (size_t)h->ncap * kStateComps;
-    StepArgs a = base_args(h);
-    a.sin = a.sout = h->d_state.p;
-    a.acc = h->d_acc.p;
-    a.vout = h->d_vout.p;
-    a.flags = h->d_flags.p;
-    a.keep_grid = 0;
-    for (int i = 0; i < n_substeps; i++) {
-        if (record && h->rec_len % K == 0) {
-            const size_t c = (size_t)(h->rec_len / K);
-            if (h->ckpt.size() <= c) h->ckpt.resize(c + 1);
-            RK(h->ckpt[c].ensure(state_floats, h->device_bytes));
-            CK(cudaMemcpyAsync(h->ckpt[c].p, h->d_state.p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice,
-                               h->stream));
+    if (!record) {
+        StepArgs a = base_args(h);
+        a.sin = a.sout = h->d_state.p;
+        a.acc = h->d_acc.p;
+        a.vout = h->d_vout.p;
+        a.flags = h->d_flags.p;
+        a.keep_grid = 0;
+        for (int i = 0; i < n_substeps; i++) {
+            if (h->opt.sort_every > 0 && h->since_sort >= h->opt.sort_every) {
+                RK(h->d_perm.ensure((size_t)h->ncap, h->device_bytes));
+                RK(sort_particles(h, h->d_perm.p));
+                a.sin = a.sout = h->d_state.p;
+            }
+            a.substep = (int)h->substep;
+            RK(run_substep(h, a));
+            h->substep++;
+            h->since_sort++;
         }
-        a.substep = (int)h->substep;
-        RK(run_substep(h, a));
-        h->substep++;
-        if (record) h->rec_len++;
+    } else if (n_substeps > 0) {
+        // Recorded substeps run in the segment slots, keeping every state
+        // and grid of the current segment: the backward then reverses the
+        // last segment without recomputing it. Earlier segments are
+        // recomputed from their checkpoints.
+        const float* cur = h->d_state.p;
+        for (int i = 0; i < n_substeps; i++) {
+            const int64_t j = h->rec_len / K;
+            const int k = (int)(h->rec_len % K);
+            if (k == 0) {
+                if (h->rec_len == 0) {
+                    // external order of the state the record starts from
+                    RK(h->d_ext_rec.ensure((size_t)h->ncap, h->device_bytes));
+                    CK(cudaMemcpyAsync(h->d_ext_rec.p, h->d_ext_of_slot.p, (size_t)h->ncap * sizeof(int),
+                                       cudaMemcpyDeviceToDevice, h->stream));
+                }
+                if (h->seg_sorted.size() <= (size_t)j) {
+                    h->seg_sorted.resize(j + 1, 0);
+                    h->seg_perm.resize(j + 1);
+                }
+                h->seg_sorted[j] = 0;
+                if (h->opt.sort_every > 0) {
+                    // segments start sorted; the backward undoes the permutation
+                    RK(copy_state(h, h->d_state.p, cur));
+                    RK(h->seg_perm[j].ensure((size_t)h->ncap, h->device_bytes));
+                    RK(sort_particles(h, h->seg_perm[j].p));
+                    h->seg_sorted[j] = 1;
+                    cur = h->d_state.p;
+                }
+                if (h->ckpt.size() <= (size_t)j) h->ckpt.resize(j + 1);
+                RK(h->ckpt[j].ensure(state_floats, h->device_bytes));
+                RK(copy_state(h, h->ckpt[j].p, cur));
+                RK(ensure_slot(h, 0));
+                RK(copy_state(h, h->seg_state[0].p, cur));
+                h->seg_valid = j;
+                h->seg_valid_len = 0;
+            }
+            RK(run_slot_substep(h, k, h->substep));
+            cur = h->seg_state[k + 1].p;
+            h->seg_valid_len = k + 1;
+            h->substep++;
+            h->rec_len++;
+        }
+        RK(copy_state(h, h->d_state.p, cur));
     }
     const int st = read_status(h);
-    if (st != MPM_OK) h->recording = false;
+    if (st != MPM_OK) {
+        h->recording = false;
+        h->seg_valid = -1;
+    }
     return st;
 }
 
@@ -788,24 +944,14 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, int devi
     const int K = h->opt.checkpoint_every;
     const int n_inst = (int)h->inst.size();
     const size_t state_floats = (size_t)h->ncap * kStateComps;
-    const int seg_cap = (int)std::min<int64_t>(K, h->rec_len);
-    RK(h->d_seg_state.ensure(state_floats * (seg_cap + 1), h->device_bytes));
-    const bool fresh_grids = h->d_seg_acc.n < (size_t)h->n_nodes * seg_cap;
-    RK(h->d_seg_acc.ensure((size_t)h->n_nodes * seg_cap, h->device_bytes));
-    RK(h->d_seg_vout.ensure((size_t)h->n_nodes * seg_cap, h->device_bytes));
-    RK(h->d_seg_flags.ensure((size_t)h->n_blocks * seg_cap, h->device_bytes));
     const bool fresh_gacc = h->d_gacc.n < (size_t)h->n_nodes;
     RK(h->d_gacc.ensure((size_t)h->n_nodes, h->device_bytes));
     RK(h->d_adj.ensure(state_floats, h->device_bytes));
     RK(h->d_gmat.ensure((size_t)n_inst * 4, h->device_bytes));
     RK(h->d_gpose.ensure((size_t)h->rec_len * n_inst * 8, h->device_bytes));
     cudaStream_t s = h->stream;
-    if (fresh_grids || !h->seg_grids_clean) {
-        CK(cudaMemsetAsync(h->d_seg_acc.p, 0, h->d_seg_acc.n * sizeof(float4), s));
-        CK(cudaMemsetAsync(h->d_seg_flags.p, 0, h->d_seg_flags.n, s));
-    }
-    if (fresh_gacc || !h->seg_grids_clean) CK(cudaMemsetAsync(h->d_gacc.p, 0, h->d_gacc.n * sizeof(float4), s));
-    h->seg_grids_clean = false;   // set again once every slot has been cleared
+    if (fresh_gacc || h->gacc_dirty) CK(cudaMemsetAsync(h->d_gacc.p, 0, h->d_gacc.n * sizeof(float4), s));
+    h->gacc_dirty = true;   // until every reversed substep has cleared its blocks
     // seed the adjoint of the final state
     const float *gx = dL_dx, *gv = dL_dv;
     if (!device_ptrs && (dL_dx || dL_dv)) {
@@ -823,38 +969,38 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, int devi
     for (int64_t j = n_seg - 1; j >= 0; j--) {
         const int64_t seg_begin = j * K;
         const int seg_len = (int)std::min<int64_t>(K, h->rec_len - seg_begin);
-        CK(cudaMemcpyAsync(h->d_seg_state.p, h->ckpt[j].p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        // recompute the segment, keeping every state and grid
-        for (int i = 0; i < seg_len; i++) {
-            StepArgs a = base_args(h);
-            a.sin = h->d_seg_state.p + state_floats * i;
-            a.sout = h->d_seg_state.p + state_floats * (i + 1);
-            a.acc = h->d_seg_acc.p + (size_t)h->n_nodes * i;
-            a.vout = h->d_seg_vout.p + (size_t)h->n_nodes * i;
-            a.flags = h->d_seg_flags.p + (size_t)h->n_blocks * i;
-            a.keep_grid = 1;
-            a.substep = (int)(h->rec_start + seg_begin + i);
-            RK(run_substep(h, a));
+        if (!(h->seg_valid == j && h->seg_valid_len == seg_len)) {
+            // recompute the segment from its checkpoint, keeping every state and grid
+            RK(ensure_slot(h, 0));
+            RK(copy_state(h, h->seg_state[0].p, h->ckpt[j].p));
+            for (int i = 0; i < seg_len; i++) RK(run_slot_substep(h, i, h->rec_start + seg_begin + i));
+            h->seg_valid = j;
+            h->seg_valid_len = seg_len;
         }
         // reverse it
         for (int i = seg_len - 1; i >= 0; i--) {
             AdjArgs A;
             std::memset(&A, 0, sizeof A);
-            A.f = base_args(h);
-            A.f.sin = A.f.sout = h->d_seg_state.p + state_floats * i;
-            A.f.acc = h->d_seg_acc.p + (size_t)h->n_nodes * i;
-            A.f.vout = h->d_seg_vout.p + (size_t)h->n_nodes * i;
-            A.f.flags = h->d_seg_flags.p + (size_t)h->n_blocks * i;
-            A.f.keep_grid = 1;
-            A.f.substep = (int)(h->rec_start + seg_begin + i);
+            A.f = slot_args(h, i, h->rec_start + seg_begin + i);
+            A.f.sout = h->seg_state[i].p;
             A.adj = h->d_adj.p;
             A.gacc = h->d_gacc.p;
             A.gmat = h->d_gmat.p;
             A.gpose = h->d_gpose.p + (size_t)(seg_begin + i) * n_inst * 8;
             RK(run_adjoint_substep(h, A));
+            h->seg_dirty[i] = 0;
+        }
+        h->seg_valid = -1;
+        if ((size_t)j < h->seg_sorted.size() && h->seg_sorted[j]) {
+            // adjoint w.r.t. the sorted segment start -> w.r.t. the state before the sort
+            RK(h->d_adj2.ensure(state_floats, h->device_bytes));
+            CK(launch_unpermute(h->d_inst.p, h->d_chunk_inst.p, h->n_chunks, h->ncap, h->seg_perm[j].p, h->d_adj.p,
+                                h->d_adj2.p, s));
+            h->launches++;
+            std::swap(h->d_adj, h->d_adj2);
         }
     }
-    h->seg_grids_clean = true;
+    h->gacc_dirty = false;
     std::vector<double> gm((size_t)n_inst * 4), gp((size_t)h->rec_len * n_inst * 8);
     CK(cudaMemcpyAsync(gm.data(), h->d_gmat.p, gm.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(gp.data(), h->d_gpose.p, gp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -919,6 +1065,7 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, int devi
         }
     }
     h->recording = false;
+    h->seg_valid = -1;
     h->have_grad = true;
     return st;
 }
@@ -927,16 +1074,16 @@ int mpm_get_state_grad(mpm_handle* h, float* gx, float* gv, float* gC, float* gF
     if (!h) return MPM_ERR_INVALID_ARG;
     if (!h->have_grad) return MPM_ERR_NO_RECORD;
     RK(set_device(h));
+    const int* ext = h->d_ext_rec.p ? h->d_ext_rec.p : h->d_ext_of_slot.p;
     if (device_ptrs) {
-        CK(launch_state_to_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, h->d_adj.p, gx, gv, gC, gF, h->stream));
+        CK(launch_state_to_ext(h->ncap, h->ncap, ext, h->d_adj.p, gx, gv, gC, gF, h->stream));
         h->launches++;
         return MPM_OK;
     }
     RK(ensure_stage(h));
     float* st = h->d_stage.p;
     const size_t n = (size_t)h->n_ext;
-    CK(launch_state_to_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, h->d_adj.p, st, st + 3 * n, st + 6 * n, st + 15 * n,
-                           h->stream));
+    CK(launch_state_to_ext(h->ncap, h->ncap, ext, h->d_adj.p, st, st + 3 * n, st + 6 * n, st + 15 * n, h->stream));
     h->launches++;
     if (gx) CK(cudaMemcpyAsync(gx, st, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     if (gv) CK(cudaMemcpyAsync(gv, st + 3 * n, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
@@ -960,6 +1107,7 @@ int mpm_set_substep(mpm_handle* h, int64_t substep) {
     if (!h || substep < 0 || substep > (1LL << 30)) return MPM_ERR_INVALID_ARG;
     h->substep = substep;
     h->recording = false;
+    h->seg_valid = -1;
     h->rec_len = 0;
     return MPM_OK;
 }
@@ -982,7 +1130,8 @@ int mpm_profile_read(mpm_handle* h, int kernel, double* total_ms, int64_t* launc
 }
 
 const char* mpm_kernel_name(int kernel) {
-    static const char* names[] = {"k_p2g", "k_grid", "k_g2p", "k_g2p_bwd", "k_grid_bwd", "k_p2g_bwd", "k_grid_clear"};
+    static const char* names[] = {"k_p2g",     "k_grid",       "k_g2p",       "k_g2p_bwd",
+                                  "k_grid_bwd", "k_p2g_bwd", "k_grid_clear", "k_slot_clear"};
     if (kernel < 0 || kernel >= (int)KernelId::Count) return "";
     return names[kernel];
 }

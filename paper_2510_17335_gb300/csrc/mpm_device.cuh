@@ -8,35 +8,42 @@
 
 #include "mpm_types.h"
 
+#if defined(__CUDACC__)
+#define MPM_HD __host__ __device__
+#else
+#define MPM_HD
+#endif
+
 namespace mpm {
 
 // ---------------------------------------------------------------------------
-// small helpers
+// small helpers (host and device: the math below is also compiled for the
+// host by a CPU test of the kernels' arithmetic)
 // ---------------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ T dsqrt(T x);
-template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
-template <typename T> __device__ __forceinline__ T dlog(T x);
-template <> __device__ __forceinline__ float dlog<float>(float x) { return logf(x); }
-template <> __device__ __forceinline__ double dlog<double>(double x) { return log(x); }
-template <typename T> __device__ __forceinline__ T dexp(T x);
-template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
-template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
-template <typename T> __device__ __forceinline__ T dlog1p(T x);
-template <> __device__ __forceinline__ float dlog1p<float>(float x) { return log1pf(x); }
-template <> __device__ __forceinline__ double dlog1p<double>(double x) { return log1p(x); }
-template <typename T> __device__ __forceinline__ T dfma(T a, T b, T c);
-template <> __device__ __forceinline__ float dfma<float>(float a, float b, float c) { return fmaf(a, b, c); }
-template <> __device__ __forceinline__ double dfma<double>(double a, double b, double c) { return fma(a, b, c); }
-template <typename T> __device__ __forceinline__ T dexpm1(T x);
-template <> __device__ __forceinline__ float dexpm1<float>(float x) { return expm1f(x); }
-template <> __device__ __forceinline__ double dexpm1<double>(double x) { return expm1(x); }
+template <typename T> MPM_HD __forceinline__ T dsqrt(T x);
+template <> MPM_HD __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <> MPM_HD __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+template <typename T> MPM_HD __forceinline__ T dlog(T x);
+template <> MPM_HD __forceinline__ float dlog<float>(float x) { return logf(x); }
+template <> MPM_HD __forceinline__ double dlog<double>(double x) { return log(x); }
+template <typename T> MPM_HD __forceinline__ T dexp(T x);
+template <> MPM_HD __forceinline__ float dexp<float>(float x) { return expf(x); }
+template <> MPM_HD __forceinline__ double dexp<double>(double x) { return exp(x); }
+template <typename T> MPM_HD __forceinline__ T dlog1p(T x);
+template <> MPM_HD __forceinline__ float dlog1p<float>(float x) { return log1pf(x); }
+template <> MPM_HD __forceinline__ double dlog1p<double>(double x) { return log1p(x); }
+template <typename T> MPM_HD __forceinline__ T dfma(T a, T b, T c);
+template <> MPM_HD __forceinline__ float dfma<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <> MPM_HD __forceinline__ double dfma<double>(double a, double b, double c) { return fma(a, b, c); }
+template <typename T> MPM_HD __forceinline__ T dexpm1(T x);
+template <> MPM_HD __forceinline__ float dexpm1<float>(float x) { return expm1f(x); }
+template <> MPM_HD __forceinline__ double dexpm1<double>(double x) { return expm1(x); }
 
 // Jacobi rotations are skipped only for an (almost) exactly zero off-diagonal:
 // H's entries are small, so any threshold tied to 1 would cap their accuracy.
-template <typename T> __device__ __forceinline__ T jacobi_tiny();
-template <> __device__ __forceinline__ float jacobi_tiny<float>() { return 1e-35f; }
-template <> __device__ __forceinline__ double jacobi_tiny<double>() { return 1e-300; }
+template <typename T> MPM_HD __forceinline__ T jacobi_tiny();
+template <> MPM_HD __forceinline__ float jacobi_tiny<float>() { return 1e-35f; }
+template <> MPM_HD __forceinline__ double jacobi_tiny<double>() { return 1e-300; }
 template <typename T> struct Sweeps;
 template <> struct Sweeps<float> { static constexpr int n = 4; };
 template <> struct Sweeps<double> { static constexpr int n = 10; };
@@ -53,7 +60,7 @@ template <> struct Sweeps<double> { static constexpr int n = 10; };
 // what the apex and yield decisions of the return mapping need in FP32.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
+MPM_HD __forceinline__ void two_sum(T a, T b, T& s, T& e) {
     s = a + b;
     const T bb = s - a;
     e = (a - (s - bb)) + (b - bb);
@@ -61,7 +68,7 @@ __device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
 
 // sum_k x_k y_k - shift, compensated
 template <typename T>
-__device__ __forceinline__ T dot3_minus(T x0, T y0, T x1, T y1, T x2, T y2, T shift) {
+MPM_HD __forceinline__ T dot3_minus(T x0, T y0, T x1, T y1, T x2, T y2, T shift) {
     const T p0 = x0 * y0, p1 = x1 * y1, p2 = x2 * y2;
     const T e0 = dfma<T>(x0, y0, -p0), e1 = dfma<T>(x1, y1, -p1), e2 = dfma<T>(x2, y2, -p2);
     T s, c1, c2, c3;
@@ -72,7 +79,7 @@ __device__ __forceinline__ T dot3_minus(T x0, T y0, T x1, T y1, T x2, T y2, T sh
 }
 
 template <typename T, int p, int q, int r>
-__device__ __forceinline__ void jacobi_rotate(T (&G)[3][3], T (&V)[3][3]) {
+MPM_HD __forceinline__ void jacobi_rotate(T (&G)[3][3], T (&V)[3][3]) {
     const T gpq = G[p][q], gpp = G[p][p], gqq = G[q][q];
     if (!(fabs(gpq) > jacobi_tiny<T>())) return;
     const T zeta = (gqq - gpp) / (T(2) * gpq);
@@ -98,7 +105,7 @@ __device__ __forceinline__ void jacobi_rotate(T (&G)[3][3], T (&V)[3][3]) {
 
 // h[k] = sigma_k^2 - 1 to full relative accuracy
 template <typename T>
-__device__ __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3], T (&V)[3][3], T (&h)[3]) {
+MPM_HD __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3], T (&V)[3][3], T (&h)[3]) {
     T G[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -216,7 +223,7 @@ struct Spectral {
 };
 
 template <typename T>
-__device__ __forceinline__ void return_map(Spectral<T>& S, T mu, T lam, T beta, T smin) {
+MPM_HD __forceinline__ void return_map(Spectral<T>& S, T mu, T lam, T beta, T smin) {
     S.tr = T(0);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -260,7 +267,7 @@ __device__ __forceinline__ void return_map(Spectral<T>& S, T mu, T lam, T beta, 
 
 // trial F -> spectral data (SVD + return mapping)
 template <typename T>
-__device__ __forceinline__ void constitutive_spectral(const T (&Ft)[3][3], T mu, T lam, T beta, T smin,
+MPM_HD __forceinline__ void constitutive_spectral(const T (&Ft)[3][3], T mu, T lam, T beta, T smin,
                                                       Spectral<T>& S) {
     svd3<T>(Ft, S.U, S.s, S.V, S.h);
     return_map<T>(S, mu, lam, beta, smin);
@@ -268,7 +275,7 @@ __device__ __forceinline__ void constitutive_spectral(const T (&Ft)[3][3], T mu,
 
 // F' = U diag(shat) V^T and tau = U diag(t) U^T
 template <typename T, typename O>
-__device__ __forceinline__ void spectral_outputs(const Spectral<T>& S, O (&Fn)[3][3], O (&tau)[3][3]) {
+MPM_HD __forceinline__ void spectral_outputs(const Spectral<T>& S, O (&Fn)[3][3], O (&tau)[3][3]) {
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
@@ -285,14 +292,14 @@ __device__ __forceinline__ void spectral_outputs(const Spectral<T>& S, O (&Fn)[3
 }
 
 // ill-conditioned or non-finite FP32 results are redone in FP64
-__device__ __forceinline__ bool needs_fp64(const Spectral<float>& S) {
+MPM_HD __forceinline__ bool needs_fp64(const Spectral<float>& S) {
     const float amax = fmaxf(fabsf(S.s[0]), fmaxf(fabsf(S.s[1]), fabsf(S.s[2])));
     const float amin = fminf(fabsf(S.s[0]), fminf(fabsf(S.s[1]), fabsf(S.s[2])));
     return !(amin >= 1e-3f * amax) || !isfinite(amax);
 }
 
 // forward constitutive step with the FP64 fallback kept out of line
-__device__ __noinline__ void constitutive_fp64(const float (&Ft)[3][3], float mu, float lam, float beta, float smin,
+MPM_HD __noinline__ void constitutive_fp64(const float (&Ft)[3][3], float mu, float lam, float beta, float smin,
                                                float (&Fn)[3][3], float (&tau)[3][3]) {
     double Fd[3][3];
 #pragma unroll
@@ -304,7 +311,7 @@ __device__ __noinline__ void constitutive_fp64(const float (&Ft)[3][3], float mu
     spectral_outputs<double, float>(S, Fn, tau);
 }
 
-__device__ __forceinline__ bool constitutive(const float (&Ft)[3][3], float mu, float lam, float beta, float smin,
+MPM_HD __forceinline__ bool constitutive(const float (&Ft)[3][3], float mu, float lam, float beta, float smin,
                                              float (&Fn)[3][3], float (&tau)[3][3]) {
     Spectral<float> S;
     constitutive_spectral<float>(Ft, mu, lam, beta, smin, S);
@@ -324,108 +331,73 @@ __device__ __forceinline__ bool constitutive(const float (&Ft)[3][3], float mu, 
 // through expm1 so that it stays exact at s_i = s_j.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ T xm1(T x) { return x == T(0) ? T(1) : x / dexpm1<T>(x); }
+MPM_HD __forceinline__ T xm1(T x) { return x == T(0) ? T(1) : x / dexpm1<T>(x); }
 template <typename T>
-__device__ __forceinline__ T em1ratio(T k, T x) { return x == T(0) ? k : dexpm1<T>(k * x) / dexpm1<T>(x); }
+MPM_HD __forceinline__ T em1ratio(T k, T x) { return x == T(0) ? k : dexpm1<T>(k * x) / dexpm1<T>(x); }
 
 template <typename T>
-__device__ __forceinline__ void constitutive_adjoint_spectral(const Spectral<T>& S, T mu, T lam, T alpha, T beta,
+MPM_HD __forceinline__ void constitutive_adjoint_spectral(const Spectral<T>& S, T mu, T lam, T alpha, T beta,
                                                               T smin, const T (&gFn)[3][3], const T (&gtau)[3][3],
                                                               T (&gFt)[3][3], T& gmu, T& glam, T& galpha) {
-    // rotate the output adjoints into the singular frames
-    T G[3][3], Tt[3][3], tmp[3][3];
+    // output adjoints in the singular frames: G = U^T gFn V, Th = U^T gtau U
+    T G[3][3], Th[3][3];
+    {
+        T a1[3][3], a2[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            T x = T(0), y = T(0);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                x += S.U[k][a] * gFn[k][b];
-                y += S.U[k][a] * gtau[k][b];
-            }
-            tmp[a][b] = x;
-            Tt[a][b] = y;   // U^T gtau (right factor below)
-        }
-    T Th[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            T x = T(0), y = T(0);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                x += tmp[a][k] * S.V[k][b];
-                y += Tt[a][k] * S.U[k][b];
-            }
-            G[a][b] = x;
-            Th[a][b] = y;
-        }
-    // Jacobians in sigma: Je = de/ds, Jsh = dshat/ds; and d/dbeta
-    T Je[3][3], Jsh[3][3], de_db[3], dsh_db[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        de_db[a] = T(0);
-        dsh_db[a] = T(0);
-#pragma unroll
-        for (int b = 0; b < 3; b++) { Je[a][b] = T(0); Jsh[a][b] = T(0); }
-    }
-    if (S.kase == 1) {
-#pragma unroll
-        for (int a = 0; a < 3; a++) { Je[a][a] = S.deps[a]; Jsh[a][a] = T(1); }
-    } else if (S.kase == 2) {
-        const T inv_nh = T(1) / S.nh;
-        T eh[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) eh[a] = S.ehat[a] * inv_nh;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
+        for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int b = 0; b < 3; b++) {
-                const T P = (a == b ? T(1) : T(0)) - T(1.0 / 3.0);
-                const T d = T(1.0 / 3.0) - beta * (eh[a] + S.tr * (P - eh[a] * eh[b]) * inv_nh);
-                Je[a][b] = d * S.deps[b];
-                Jsh[a][b] = S.shat[a] * Je[a][b];
+                a1[a][b] = S.U[0][a] * gFn[0][b] + S.U[1][a] * gFn[1][b] + S.U[2][a] * gFn[2][b];
+                a2[a][b] = S.U[0][a] * gtau[0][b] + S.U[1][a] * gtau[1][b] + S.U[2][a] * gtau[2][b];
             }
-            de_db[a] = -S.tr * eh[a];
-            dsh_db[a] = S.shat[a] * de_db[a];
-        }
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                G[a][b] = a1[a][0] * S.V[0][b] + a1[a][1] * S.V[1][b] + a1[a][2] * S.V[2][b];
+                Th[a][b] = a2[a][0] * S.U[0][b] + a2[a][1] * S.U[1][b] + a2[a][2] * S.U[2][b];
+            }
     }
-    // t = 2 mu e + lam (sum e)
-    T Jt[3][3], dt_db[3];
-    const T sdb = de_db[0] + de_db[1] + de_db[2];
-#pragma unroll
-    for (int b = 0; b < 3; b++) {
-        const T cs = Je[0][b] + Je[1][b] + Je[2][b];
-#pragma unroll
-        for (int a = 0; a < 3; a++) Jt[a][b] = T(2) * mu * Je[a][b] + lam * cs;
-    }
-#pragma unroll
-    for (int a = 0; a < 3; a++) dt_db[a] = T(2) * mu * de_db[a] + lam * sdb;
-    T K[3][3];
-#pragma unroll
-    for (int b = 0; b < 3; b++) {
-        T g = T(0);
-#pragma unroll
-        for (int a = 0; a < 3; a++) g += G[a][a] * Jsh[a][b] + Th[a][a] * Jt[a][b];
-#pragma unroll
-        for (int a = 0; a < 3; a++) K[a][b] = (a == b) ? g : T(0);
-    }
-    T gb = T(0);
+    // singular-value adjoints as vector-Jacobian products of
+    // t = 2 mu e + lam (sum e) 1, shat = exp(e) (case 2) or s (case 1)
+    const T tb[3] = {Th[0][0], Th[1][1], Th[2][2]};
+    const T stb = tb[0] + tb[1] + tb[2];
     const T se = S.e[0] + S.e[1] + S.e[2];
+    gmu += T(2) * (tb[0] * S.e[0] + tb[1] * S.e[1] + tb[2] * S.e[2]);
+    glam += stb * se;
+    T sb[3] = {T(0), T(0), T(0)};
+    if (S.kase == 1) {
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        gb += G[a][a] * dsh_db[a] + Th[a][a] * dt_db[a];
-        gmu += Th[a][a] * T(2) * S.e[a];
-        glam += Th[a][a] * se;
-    }
-    if (S.kase == 2) {
-        const T c = T(1) + T(1.5) * lam / mu;
+        for (int i = 0; i < 3; i++) sb[i] = G[i][i] + (T(2) * mu * tb[i] + lam * stb) * S.deps[i];
+    } else if (S.kase == 2) {
+        const T inv_nh = T(1) / S.nh;
+        T eb[3], eh[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            eb[i] = T(2) * mu * tb[i] + lam * stb + S.shat[i] * G[i][i];
+            eh[i] = S.ehat[i] * inv_nh;
+        }
+        const T sE = eb[0] + eb[1] + eb[2];
+        const T eE = eb[0] * eh[0] + eb[1] * eh[1] + eb[2] * eh[2];
+        const T third = sE * T(1.0 / 3.0);
+        // e = (tr/3) 1 - beta tr ehat: eps_bar = (sum eb)/3 1 - beta [(eb.eh) 1 + tr/nh (P eb - (eb.eh) eh)]
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const T epsb = third - beta * (eE + S.tr * inv_nh * ((eb[i] - third) - eE * eh[i]));
+            sb[i] = epsb * S.deps[i];
+        }
+        // beta = (3 lam + 2 mu)/(2 mu) alpha and de/dbeta = -tr ehat
+        const T gb = -S.tr * eE;
         gmu += gb * alpha * (T(-1.5) * lam / (mu * mu));
         glam += gb * alpha * (T(1.5) / mu);
-        galpha += gb * c;
+        galpha += gb * (T(1) + T(1.5) * lam / mu);
     }
-    // off-diagonal pairs
+    T K[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) K[a][b] = (a == b) ? sb[a] : T(0);
+    // off-diagonal pairs: divided differences of shat and t
 #pragma unroll
     for (int pr = 0; pr < 3; pr++) {
         const int i = (pr == 2) ? 1 : 0;
@@ -435,7 +407,8 @@ __device__ __forceinline__ void constitutive_adjoint_spectral(const Spectral<T>&
         const T dsig = si - sj;
         T sum = si + sj;
         if (fabs(sum) < T(1e-30)) sum = T(1e-30);
-        const bool close = fabs(dsig) <= T(1e-6) * fmax(fabs(si), fabs(sj));
+        // clamped singular values (below smin) only: plain quotients, 0 when equal
+        const bool sep = fabs(dsig) > T(1e-30);
         T ds, dd, q1;
         if (S.kase == 0) {
             ds = T(0);
@@ -444,18 +417,15 @@ __device__ __forceinline__ void constitutive_adjoint_spectral(const Spectral<T>&
         } else if (S.kase == 1) {
             ds = T(1);
             dd = T(1);
-            if (smooth)
-                q1 = T(2) * mu * xm1<T>(S.eps[i] - S.eps[j]) / sj;
-            else
-                q1 = close ? (Jt[i][i] - Jt[i][j]) : (S.t[i] - S.t[j]) / dsig;
+            q1 = smooth ? T(2) * mu * xm1<T>(S.eps[i] - S.eps[j]) / sj : (sep ? (S.t[i] - S.t[j]) / dsig : T(0));
         } else {
             if (smooth) {
                 const T D = S.eps[i] - S.eps[j];
                 ds = S.shat[j] / sj * em1ratio<T>(S.kappa, D);
                 q1 = T(2) * mu * S.kappa * xm1<T>(D) / sj;
             } else {
-                ds = close ? (Jsh[i][i] - Jsh[i][j]) : (S.shat[i] - S.shat[j]) / dsig;
-                q1 = close ? (Jt[i][i] - Jt[i][j]) : (S.t[i] - S.t[j]) / dsig;
+                ds = sep ? (S.shat[i] - S.shat[j]) / dsig : T(0);
+                q1 = sep ? (S.t[i] - S.t[j]) / dsig : T(0);
             }
             dd = (S.shat[i] + S.shat[j]) / sum;
         }
@@ -468,26 +438,16 @@ __device__ __forceinline__ void constitutive_adjoint_spectral(const Spectral<T>&
     }
     // gFt = U K V^T
 #pragma unroll
-    for (int a = 0; a < 3; a++)
+    for (int a = 0; a < 3; a++) {
+        T r0 = S.U[a][0] * K[0][0] + S.U[a][1] * K[1][0] + S.U[a][2] * K[2][0];
+        T r1 = S.U[a][0] * K[0][1] + S.U[a][1] * K[1][1] + S.U[a][2] * K[2][1];
+        T r2 = S.U[a][0] * K[0][2] + S.U[a][1] * K[1][2] + S.U[a][2] * K[2][2];
 #pragma unroll
-        for (int b = 0; b < 3; b++) {
-            T x = T(0);
-#pragma unroll
-            for (int k = 0; k < 3; k++) x += S.U[a][k] * K[k][b];
-            tmp[a][b] = x;
-        }
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            T x = T(0);
-#pragma unroll
-            for (int k = 0; k < 3; k++) x += tmp[a][k] * S.V[b][k];
-            gFt[a][b] = x;
-        }
+        for (int b = 0; b < 3; b++) gFt[a][b] = r0 * S.V[b][0] + r1 * S.V[b][1] + r2 * S.V[b][2];
+    }
 }
 
-__device__ __noinline__ void constitutive_adjoint_fp64(const float (&Ft)[3][3], float mu, float lam, float alpha,
+MPM_HD __noinline__ void constitutive_adjoint_fp64(const float (&Ft)[3][3], float mu, float lam, float alpha,
                                                        float beta, float smin, const float (&gFn)[3][3],
                                                        const float (&gtau)[3][3], float (&tau)[3][3],
                                                        float (&gFt)[3][3], float& gmu, float& glam, float& galpha) {
@@ -587,7 +547,7 @@ __device__ __forceinline__ Pose load_pose(const InstDev& I, int substep) {
 }
 
 // inside test; on success n (world) and nl (local) face normals
-__device__ __forceinline__ bool shovel_inside(const InstDev& I, const Pose& P, float cs, float sn, const float (&q)[3],
+MPM_HD __forceinline__ bool shovel_inside(const InstDev& I, const Pose& P, float cs, float sn, const float (&q)[3],
                                               float (&n)[3], float (&nl)[3]) {
     const float r0 = q[0] - P.c[0], r1 = q[1] - P.c[1], r2 = q[2] - P.c[2];
     const float l0 = cs * r0 - sn * r1;
@@ -595,20 +555,22 @@ __device__ __forceinline__ bool shovel_inside(const InstDev& I, const Pose& P, f
     const float l2 = r2;
     const float d0 = fabsf(l0) - I.sh[0], d1 = fabsf(l1) - I.sh[1], d2 = fabsf(l2) - I.sh[2];
     if (!(d0 < 0.0f && d1 < 0.0f && d2 < 0.0f)) return false;
+    // nearest face; faces whose distances are within 1e-7 m of each other
+    // (an edge or corner) resolve to the lowest axis index
     int a = 0;
     float dm = d0;
-    if (d1 > dm) { a = 1; dm = d1; }
-    if (d2 > dm) { a = 2; }
+    if (d1 > dm + 1e-7f) { a = 1; dm = d1; }
+    if (d2 > dm + 1e-7f) { a = 2; }
     nl[0] = nl[1] = nl[2] = 0.0f;
     const float lv = (a == 0) ? l0 : ((a == 1) ? l1 : l2);
-    nl[a] = lv >= 0.0f ? 1.0f : -1.0f;
+    nl[a] = lv > -1e-7f ? 1.0f : -1.0f;   // within 1e-7 m of the mid-plane: the + face
     n[0] = cs * nl[0] + sn * nl[1];
     n[1] = -sn * nl[0] + cs * nl[1];
     n[2] = nl[2];
     return true;
 }
 
-__device__ __forceinline__ void shovel_project(const InstDev& I, const Pose& P, float cs, float sn, const float (&q)[3],
+MPM_HD __forceinline__ void shovel_project(const InstDev& I, const Pose& P, float cs, float sn, const float (&q)[3],
                                                float (&v)[3]) {
     float n[3], nl[3];
     if (!shovel_inside(I, P, cs, sn, q, n, nl)) return;
@@ -627,7 +589,7 @@ __device__ __forceinline__ void shovel_project(const InstDev& I, const Pose& P, 
 }
 
 // reverse of shovel_project: g (adjoint of the output) -> adds to gv, gq, gp[8]
-__device__ __forceinline__ void shovel_project_adj(const InstDev& I, const Pose& P, float cs, float sn,
+MPM_HD __forceinline__ void shovel_project_adj(const InstDev& I, const Pose& P, float cs, float sn,
                                                    const float (&q)[3], const float (&v)[3], const float (&g)[3],
                                                    float (&gv)[3], float (&gq)[3], float (&gp)[8]) {
     float n[3], nl[3];
@@ -686,13 +648,17 @@ __device__ __forceinline__ void shovel_project_adj(const InstDev& I, const Pose&
     gp[1] -= gr1;
 }
 
-__device__ __forceinline__ float clipf(float g, float c) { return fminf(fmaxf(g, -c), c); }
+MPM_HD __forceinline__ float clipf(float g, float c) { return fminf(fmaxf(g, -c), c); }
 
 // ---------------------------------------------------------------------------
-// FP64 block reduction of `NV` values per thread into dst (atomicAdd)
+// Block reduction of NV values per thread into dst (FP64 atomicAdd): each
+// warp sums its 32 lanes in FP32 (a 32-term sum stays accurate to ~1e-6
+// relative), the warp sums are then added in FP64 across the block and the
+// blocks meet in FP64 atomics. FP64 shuffles would cost ~20 FP64 adds per
+// thread at the FP64 pipe's 1/64 rate.
 // ---------------------------------------------------------------------------
 template <int NV>
-__device__ __forceinline__ void block_reduce_add(double (&v)[NV], double* dst, double* sred /* [NV*32] */) {
+__device__ __forceinline__ void block_reduce_add(float (&v)[NV], double* dst, double* sred /* [NV*32] */) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < NV; k++)
@@ -700,15 +666,111 @@ __device__ __forceinline__ void block_reduce_add(double (&v)[NV], double* dst, d
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < NV; k++) sred[k * 32 + warp] = v[k];
+        for (int k = 0; k < NV; k++) sred[k * 32 + warp] = (double)v[k];
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x < NV) {
+        double x = 0.0;
+        for (int w = 0; w < nw; w++) x += sred[threadIdx.x * 32 + w];
+        if (x != 0.0) atomicAdd(dst + threadIdx.x, x);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory tile for the 27-node scatters (P2G and the G2P adjoint).
+// A CTA takes the bounding box of its particles' stencils; if it holds at
+// most kTileNodes nodes, contributions are summed in shared memory and the
+// CTA then adds every touched node to the global grid with one float4
+// atomic. Otherwise (particles of the chunk far apart) the CTA scatters
+// straight into the global grid. The decision is uniform per CTA.
+// ---------------------------------------------------------------------------
+constexpr int kTileNodes = 1024;
+
+struct TileSmem {
+    float c[4][kTileNodes];   // the four accumulated components, SoA
+    int lo[3], dim[3];
+    int tiled;
+};
+
+// bounding box of the stencils of the active threads' particles; all
+// threads of the CTA must call it
+__device__ __forceinline__ void tile_begin(TileSmem& T, bool active, const Stencil& st, int nthreads) {
+    int lo[3], hi[3];
 #pragma unroll
-        for (int k = 0; k < NV; k++) {
-            double x = lane < nw ? sred[k * 32 + lane] : 0.0;
+    for (int a = 0; a < 3; a++) {
+        lo[a] = active ? st.base[a] : 0x3fffffff;
+        hi[a] = active ? st.base[a] : -0x3fffffff;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0 && x != 0.0) atomicAdd(dst + k, x);
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    }
+    __shared__ int s_lo[3][32], s_hi[3][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (nthreads + 31) >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < 3; a++) { s_lo[a][warp] = lo[a]; s_hi[a][warp] = hi[a]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int n = 1;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            int l = s_lo[a][0], h = s_hi[a][0];
+            for (int w = 1; w < nw; w++) { l = min(l, s_lo[a][w]); h = max(h, s_hi[a][w]); }
+            T.lo[a] = l;
+            T.dim[a] = (h >= l) ? h - l + 3 : 0;
+            n *= T.dim[a];
+        }
+        T.tiled = (n > 0 && n <= kTileNodes) ? 1 : 0;
+    }
+    __syncthreads();
+    if (T.tiled) {
+        const int n = T.dim[0] * T.dim[1] * T.dim[2];
+        for (int i = threadIdx.x; i < n; i += nthreads) {
+            T.c[0][i] = 0.f; T.c[1][i] = 0.f; T.c[2][i] = 0.f; T.c[3][i] = 0.f;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void red_shared(float* p, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
+}
+
+// add val to node base + (i, j, k): into the tile, or to the global grid
+__device__ __forceinline__ void tile_add(TileSmem& T, float4* grid, int gofs, const Stencil& st, int i, int j, int k,
+                                         float4 val, int ncomp) {
+    if (T.tiled) {
+        const int t = ((st.base[0] + i - T.lo[0]) * T.dim[1] + (st.base[1] + j - T.lo[1])) * T.dim[2] +
+                      (st.base[2] + k - T.lo[2]);
+        red_shared(&T.c[0][t], val.x);
+        red_shared(&T.c[1][t], val.y);
+        red_shared(&T.c[2][t], val.z);
+        if (ncomp == 4) red_shared(&T.c[3][t], val.w);
+    } else {
+        atomicAdd(grid + gofs, val);
+    }
+}
+
+// flush a tile to the global grid (blocked layout of instance I); marks the
+// grid blocks that received mass when flags != nullptr
+__device__ __forceinline__ void tile_flush(TileSmem& T, const InstDev& I, float4* grid, unsigned char* flags,
+                                           int nthreads) {
+    __syncthreads();
+    if (!T.tiled) return;
+    const int n = T.dim[0] * T.dim[1] * T.dim[2];
+    const int sx = I.nb[1] * I.nb[2] * 64, sy = I.nb[2] * 64;
+    for (int t = threadIdx.x; t < n; t += nthreads) {
+        const float4 v = make_float4(T.c[0][t], T.c[1][t], T.c[2][t], T.c[3][t]);
+        if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+        const int iz = T.lo[2] + t % T.dim[2];
+        const int iy = T.lo[1] + (t / T.dim[2]) % T.dim[1];
+        const int ix = T.lo[0] + t / (T.dim[1] * T.dim[2]);
+        const int ofs = (ix >> 2) * sx + (ix & 3) * 16 + (iy >> 2) * sy + (iy & 3) * 4 + (iz >> 2) * 64 + (iz & 3);
+        atomicAdd(grid + I.node_off + ofs, v);
+        if (flags) {
+            unsigned char* f = flags + I.blk_off + ((ix >> 2) * I.nb[1] + (iy >> 2)) * I.nb[2] + (iz >> 2);
+            if (*f == 0) *f = 1;
         }
     }
 }

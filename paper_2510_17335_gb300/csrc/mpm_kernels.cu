@@ -36,79 +36,88 @@ __device__ __forceinline__ void mark_blocks(const InstDev& I, const Stencil& st,
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kChunk) k_p2g(StepArgs a) {
+__global__ void __launch_bounds__(kChunk, 3) k_p2g(StepArgs a) {
+    __shared__ TileSmem T;
     const int inst = a.chunk_inst[blockIdx.x];
     const InstDev& I = a.inst[inst];
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
-    if (p - I.pbeg >= I.n) return;
+    const bool active = p - I.pbeg < I.n;
     const long long N = a.ncap;
-    float x[3], v[3], C[3][3], F[3][3];
+    float x[3] = {0.5f, 0.5f, 0.5f};
+    if (active) {
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        x[k] = ld(a.sin, N, kX + k, p);
-        v[k] = ld(a.sin, N, kV + k, p);
+        for (int k = 0; k < 3; k++) x[k] = ld(a.sin, N, kX + k, p);
     }
-#pragma unroll
-    for (int r = 0; r < 3; r++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            C[r][c] = ld(a.sin, N, kC + 3 * r + c, p);
-            F[r][c] = ld(a.sin, N, kF + 3 * r + c, p);
-        }
-    // trial deformation gradient (I + dt C) F
-    float Ft[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; r++)
-#pragma unroll
-        for (int c = 0; c < 3; c++)
-            Ft[r][c] = F[r][c] + I.dt * (C[r][0] * F[0][c] + C[r][1] * F[1][c] + C[r][2] * F[2][c]);
-    float Fn[3][3], tau[3][3];
-    if (constitutive(Ft, I.mu, I.lam, I.beta, I.smin, Fn, tau)) atomicAdd(a.fp64_count, 1ull);
-    bool finite = true;
-#pragma unroll
-    for (int r = 0; r < 3; r++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            a.sout[(kF + 3 * r + c) * N + p] = Fn[r][c];
-            finite = finite && isfinite(Fn[r][c]);
-        }
-    if (!finite) atomicOr(a.status, kStatusNonFinite);
-    // affine momentum: stress term of MLS-MPM plus APIC
-    float A[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; r++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) A[r][c] = I.stress_scale * tau[r][c] + I.mp * C[r][c];
     Stencil st;
-    if (!make_stencil(I, x, st)) atomicOr(a.status, kStatusDomain);
-    int ox[3], oy[3], oz[3];
-    node_offsets(I, st, ox, oy, oz);
-    float mv[3];
+    const bool inside = make_stencil(I, x, st);
+    if (active && !inside) atomicOr(a.status, kStatusDomain);
+    if (a.tile) tile_begin(T, active, st, kChunk);
+    else if (threadIdx.x == 0) T.tiled = 0;
+    if (!a.tile) __syncthreads();
+    if (active) {
+        float v[3], C[3][3], F[3][3];
 #pragma unroll
-    for (int k = 0; k < 3; k++) mv[k] = I.mp * v[k];
-    // A d with d = (o - f) dx, built per axis
-    float4* acc = a.acc + I.node_off;
+        for (int k = 0; k < 3; k++) v[k] = ld(a.sin, N, kV + k, p);
 #pragma unroll
-    for (int i = 0; i < 3; i++) {
-        const float dxi = (float(i) - st.fx[0]) * I.dx;
+        for (int r = 0; r < 3; r++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            const float dyj = (float(j) - st.fx[1]) * I.dx;
-            const float wij = st.w[0][i] * st.w[1][j];
+            for (int c = 0; c < 3; c++) {
+                C[r][c] = ld(a.sin, N, kC + 3 * r + c, p);
+                F[r][c] = ld(a.sin, N, kF + 3 * r + c, p);
+            }
+        // trial deformation gradient (I + dt C) F
+        float Ft[3][3];
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                const float dzk = (float(k) - st.fx[2]) * I.dx;
-                const float W = wij * st.w[2][k];
-                float4 val;
-                val.x = W * I.mp;
-                val.y = W * (mv[0] + A[0][0] * dxi + A[0][1] * dyj + A[0][2] * dzk);
-                val.z = W * (mv[1] + A[1][0] * dxi + A[1][1] * dyj + A[1][2] * dzk);
-                val.w = W * (mv[2] + A[2][0] * dxi + A[2][1] * dyj + A[2][2] * dzk);
-                atomicAdd(acc + ox[i] + oy[j] + oz[k], val);
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                Ft[r][c] = F[r][c] + I.dt * (C[r][0] * F[0][c] + C[r][1] * F[1][c] + C[r][2] * F[2][c]);
+        float Fn[3][3], tau[3][3];
+        if (constitutive(Ft, I.mu, I.lam, I.beta, I.smin, Fn, tau)) atomicAdd(a.fp64_count, 1ull);
+        bool finite = true;
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                a.sout[(kF + 3 * r + c) * N + p] = Fn[r][c];
+                finite = finite && isfinite(Fn[r][c]);
+            }
+        if (!finite) atomicOr(a.status, kStatusNonFinite);
+        // affine momentum: stress term of MLS-MPM plus APIC
+        float A[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) A[r][c] = I.stress_scale * tau[r][c] + I.mp * C[r][c];
+        int ox[3], oy[3], oz[3];
+        node_offsets(I, st, ox, oy, oz);
+        float mv[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) mv[k] = I.mp * v[k];
+        float4* acc = a.acc + I.node_off;
+#pragma unroll 1
+        for (int i = 0; i < 3; i++) {
+            const float dxi = (float(i) - st.fx[0]) * I.dx;
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const float dyj = (float(j) - st.fx[1]) * I.dx;
+                const float wij = st.w[0][i] * st.w[1][j];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const float dzk = (float(k) - st.fx[2]) * I.dx;
+                    const float W = wij * st.w[2][k];
+                    float4 val;
+                    val.x = W * I.mp;
+                    val.y = W * (mv[0] + A[0][0] * dxi + A[0][1] * dyj + A[0][2] * dzk);
+                    val.z = W * (mv[1] + A[1][0] * dxi + A[1][1] * dyj + A[1][2] * dzk);
+                    val.w = W * (mv[2] + A[2][0] * dxi + A[2][1] * dyj + A[2][2] * dzk);
+                    tile_add(T, acc, ox[i] + oy[j] + oz[k], st, i, j, k, val, 4);
+                }
             }
         }
+        if (!T.tiled) mark_blocks(I, st, a.flags);
     }
-    mark_blocks(I, st, a.flags);
+    tile_flush(T, I, a.acc, a.flags, kChunk);
 }
 
 // velocity update of one node (gravity, walls); returns false for empty nodes
@@ -160,7 +169,7 @@ __global__ void __launch_bounds__(256) k_grid(StepArgs a) {
     if (!a.keep_grid && lane == 0) a.flags[gw] = 0;
 }
 
-__global__ void __launch_bounds__(kChunk) k_g2p(StepArgs a) {
+__global__ void __launch_bounds__(kChunk, 4) k_g2p(StepArgs a) {
     const int inst = a.chunk_inst[blockIdx.x];
     const InstDev& I = a.inst[inst];
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
@@ -175,7 +184,7 @@ __global__ void __launch_bounds__(kChunk) k_g2p(StepArgs a) {
     node_offsets(I, st, ox, oy, oz);
     const float4* vg = a.vout + I.node_off;
     float v[3] = {0.0f, 0.0f, 0.0f}, B[3][3] = {{0.0f}};
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < 3; i++) {
         const float di = float(i) - st.fx[0];
 #pragma unroll
@@ -233,8 +242,9 @@ __global__ void __launch_bounds__(kChunk) k_g2p(StepArgs a) {
 // ---------------------------------------------------------------------------
 // adjoint
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kChunk) k_g2p_bwd(AdjArgs A) {
+__global__ void __launch_bounds__(kChunk, 3) k_g2p_bwd(AdjArgs A) {
     __shared__ double sred[8 * 32];
+    __shared__ TileSmem T;
     const StepArgs& a = A.f;
     const int inst = a.chunk_inst[blockIdx.x];
     const InstDev& I = a.inst[inst];
@@ -242,11 +252,20 @@ __global__ void __launch_bounds__(kChunk) k_g2p_bwd(AdjArgs A) {
     const bool active = p - I.pbeg < I.n;
     const long long N = a.ncap;
     float gp[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float x[3] = {0.5f, 0.5f, 0.5f};
     if (active) {
-        float x[3], gx[3], gv[3], gC[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) x[k] = ld(a.sin, N, kX + k, p);
+    }
+    Stencil st;
+    make_stencil(I, x, st);
+    if (a.tile) tile_begin(T, active, st, kChunk);
+    else if (threadIdx.x == 0) T.tiled = 0;
+    if (!a.tile) __syncthreads();
+    if (active) {
+        float gx[3], gv[3], gC[3][3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            x[k] = ld(a.sin, N, kX + k, p);
             gx[k] = A.adj[(kX + k) * N + p];
             gv[k] = A.adj[(kV + k) * N + p];
             if (a.clip > 0.f) { gx[k] = clipf(gx[k], a.clip); gv[k] = clipf(gv[k], a.clip); }
@@ -255,8 +274,6 @@ __global__ void __launch_bounds__(kChunk) k_g2p_bwd(AdjArgs A) {
         for (int r = 0; r < 3; r++)
 #pragma unroll
             for (int c = 0; c < 3; c++) gC[r][c] = A.adj[(kC + 3 * r + c) * N + p];
-        Stencil st;
-        make_stencil(I, x, st);
         int ox[3], oy[3], oz[3];
         node_offsets(I, st, ox, oy, oz);
         const float4* vg = a.vout + I.node_off;
@@ -288,7 +305,7 @@ __global__ void __launch_bounds__(kChunk) k_g2p_bwd(AdjArgs A) {
         // adjoint of the APIC gather: scatter into the grid velocity adjoint
         const float kap = 4.0f * I.inv_dx * I.inv_dx;
         float4* ga = A.gacc + I.node_off;
-#pragma unroll
+#pragma unroll 1
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++)
@@ -309,7 +326,7 @@ __global__ void __launch_bounds__(kChunk) k_g2p_bwd(AdjArgs A) {
                     contrib.y = W * (gvn[1] + kap * Cd[1]);
                     contrib.z = W * (gvn[2] + kap * Cd[2]);
                     contrib.w = 0.f;
-                    atomicAdd(ga + ox[i] + oy[j] + oz[k], contrib);
+                    tile_add(T, ga, ox[i] + oy[j] + oz[k], st, i, j, k, contrib, 3);
                     const float Wbar = vi[0] * (gvn[0] + kap * Cd[0]) + vi[1] * (gvn[1] + kap * Cd[1]) +
                                        vi[2] * (gvn[2] + kap * Cd[2]);
 #pragma unroll
@@ -321,12 +338,8 @@ __global__ void __launch_bounds__(kChunk) k_g2p_bwd(AdjArgs A) {
 #pragma unroll
         for (int k = 0; k < 3; k++) A.adj[(kX + k) * N + p] = gx[k];
     }
-    if (I.pcoll && I.shovel_on) {
-        double gd[8];
-#pragma unroll
-        for (int k = 0; k < 8; k++) gd[k] = gp[k];
-        block_reduce_add<8>(gd, A.gpose + 8 * inst, sred);
-    }
+    tile_flush(T, I, A.gacc, nullptr, kChunk);
+    if (I.pcoll && I.shovel_on) block_reduce_add<8>(gp, A.gpose + 8 * inst, sred);
 }
 
 __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
@@ -389,10 +402,10 @@ __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
         if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
             for (int k = 0; k < 8; k++) {
-                double x = gp[k];
+                float x = gp[k];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-                if (lane == 0 && x != 0.0) atomicAdd(A.gpose + 8 * inst + k, x);
+                if (lane == 0 && x != 0.f) atomicAdd(A.gpose + 8 * inst + k, (double)x);
             }
         }
     }
@@ -449,7 +462,7 @@ __global__ void __launch_bounds__(kChunk) k_p2g_bwd(AdjArgs A) {
         node_offsets(I, st, ox, oy, oz);
         const float4* ga = A.gacc + I.node_off;
         float gv[3] = {0.f, 0.f, 0.f}, gA[3][3] = {{0.f}};
-#pragma unroll
+#pragma unroll 1
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++)
@@ -521,7 +534,7 @@ __global__ void __launch_bounds__(kChunk) k_p2g_bwd(AdjArgs A) {
             }
         if (!finite) atomicOr(a.status, kStatusNonFinite);
     }
-    double gd[4] = {gmu, glam, galpha, gmp};
+    float gd[4] = {gmu, glam, galpha, gmp};
     block_reduce_add<4>(gd, A.gmat + 4 * inst, sred);
 }
 
@@ -534,8 +547,10 @@ __global__ void __launch_bounds__(256) k_grid_clear(AdjArgs A) {
     const InstDev& I = a.inst[a.block_inst[gw]];
     const long long base = I.node_off + (long long)(gw - I.blk_off) * 64;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    A.gacc[base + lane] = z;
-    A.gacc[base + lane + 32] = z;
+    if (A.gacc) {
+        A.gacc[base + lane] = z;
+        A.gacc[base + lane + 32] = z;
+    }
     a.acc[base + lane] = z;
     a.acc[base + lane + 32] = z;
     __syncwarp();
@@ -617,8 +632,16 @@ __global__ void __launch_bounds__(kChunk) k_loss_mse(const InstDev* inst, const 
         }
         l /= double(I.n);
     }
-    double v1[1] = {l};
-    block_reduce_add<1>(v1, loss + ii, sred);
+    // per-particle terms in FP64, one FP64 warp sum (the loss is reported in FP64)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0;
+        for (int w = 0; w < kChunk / 32; w++) x += sred[w];
+        if (x != 0.0) atomicAdd(loss + ii, x);
+    }
 }
 
 // total grid mass per instance after the last grid update (vout.w = m)
@@ -634,6 +657,131 @@ __global__ void __launch_bounds__(256) k_grid_mass(const InstDev* inst, const in
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
     if (lane == 0 && m != 0.0) atomicAdd(mass + ii, m);
+}
+
+// ---------------------------------------------------------------------------
+// particle sort by cell (counting sort over the cells of every instance;
+// the order inside a cell is the order in which the atomics hand out ranks)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kChunk) k_sort_keys(const InstDev* inst, const int* chunk_inst, long long ncap,
+                                                     const float* s, int* key, int* rank, int* bcount) {
+    const InstDev& I = inst[chunk_inst[blockIdx.x]];
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (p - I.pbeg >= I.n) return;
+    float x[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) x[k] = s[(kX + k) * ncap + p];
+    Stencil st;
+    make_stencil(I, x, st);
+    // key: the particle's base cell, blocks in order and cells inside a block
+    // in (x, y, z) order, so that a warp's particles share stencil nodes
+    const int blk = I.blk_off + ((st.base[0] >> 2) * I.nb[1] + (st.base[1] >> 2)) * I.nb[2] + (st.base[2] >> 2);
+    const int b = blk * 64 + ((st.base[0] & 3) * 4 + (st.base[1] & 3)) * 4 + (st.base[2] & 3);
+    key[p] = b;
+    rank[p] = atomicAdd(bcount + b, 1);
+}
+
+// exclusive scan of n ints: per-CTA scans of 1024, a scan of the CTA sums, an add
+__global__ void __launch_bounds__(1024) k_scan_local(const int* in, int* out, int* part, int n) {
+    __shared__ int warp_tot[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = i < n ? in[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const int excl = x - v + (w > 0 ? warp_tot[w - 1] : 0);
+    if (i < n) out[i] = excl;
+    if (threadIdx.x == 1023) part[blockIdx.x] = warp_tot[31];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_parts(int* part, int nparts) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < nparts; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < nparts ? part[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int t = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        const int excl = x - v + (w > 0 ? warp_tot[w - 1] : 0) + carry;
+        if (i < nparts) part[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_tot[31];
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_add(int* out, const int* part, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += part[i / 1024];
+}
+
+// new slot of every particle; perm[new] = old, ext carried along
+__global__ void __launch_bounds__(kChunk) k_sort_perm(const InstDev* inst, const int* chunk_inst, const int* key,
+                                                     const int* rank, const int* bscan, const int* ext_old, int* perm,
+                                                     int* ext_new) {
+    const InstDev& I = inst[chunk_inst[blockIdx.x]];
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (p - I.pbeg >= I.n) return;
+    const long long q = I.pbeg + (bscan[key[p]] - I.ext_off) + rank[p];
+    perm[q] = (int)p;
+    ext_new[q] = ext_old[p];
+}
+
+// dst[q] = src[perm[q]] (gather into the sorted order), all 24 components
+__global__ void __launch_bounds__(kChunk) k_permute(const InstDev* inst, const int* chunk_inst, long long ncap,
+                                                   const int* perm, const float* src, float* dst) {
+    const InstDev& I = inst[chunk_inst[blockIdx.x]];
+    const long long q = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (q - I.pbeg >= I.n) return;
+    const long long p = perm[q];
+#pragma unroll 8
+    for (int c = 0; c < kStateComps; c++) dst[c * ncap + q] = src[c * ncap + p];
+}
+
+// dst[perm[q]] = src[q] (back to the order before the sort), all 24 components
+__global__ void __launch_bounds__(kChunk) k_unpermute(const InstDev* inst, const int* chunk_inst, long long ncap,
+                                                     const int* perm, const float* src, float* dst) {
+    const InstDev& I = inst[chunk_inst[blockIdx.x]];
+    const long long q = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (q - I.pbeg >= I.n) return;
+    const long long p = perm[q];
+#pragma unroll 8
+    for (int c = 0; c < kStateComps; c++) dst[c * ncap + p] = src[c * ncap + q];
 }
 
 }  // namespace mpm
@@ -658,6 +806,12 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
         case KernelId::GridBwd: k_grid_bwd<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
         case KernelId::P2GBwd: k_p2g_bwd<<<a.n_chunks, kChunk, 0, s>>>(A); break;
         case KernelId::GridClear: k_grid_clear<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
+        case KernelId::SlotClear: {
+            AdjArgs C = A;
+            C.gacc = nullptr;
+            k_grid_clear<<<grid_ctas(a.n_blocks), 256, 0, s>>>(C);
+            break;
+        }
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -681,6 +835,31 @@ cudaError_t launch_state_to_ext(long long ncap, long long nslots, const int* ext
                                 float* v, float* C, float* F, cudaStream_t st) {
     if (nslots == 0) return cudaSuccess;
     k_state_to_ext<<<(unsigned)((nslots + 255) / 256), 256, 0, st>>>(ncap, nslots, ext_of_slot, s, x, v, C, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap, int n_keys,
+                        const float* state, float* state_out, const int* ext_old, int* ext_new, int* key, int* rank,
+                        int* bcount, int* bscan, int* part, int* perm, cudaStream_t st) {
+    if (n_chunks == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(bcount, 0, (size_t)n_keys * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_sort_keys<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, ncap, state, key, rank, bcount);
+    const int nparts = (n_keys + 1023) / 1024;
+    k_scan_local<<<nparts, 1024, 0, st>>>(bcount, bscan, part, n_keys);
+    k_scan_parts<<<1, 1024, 0, st>>>(part, nparts);
+    k_scan_add<<<(n_keys + 255) / 256, 256, 0, st>>>(bscan, part, n_keys);
+    e = cudaMemcpyAsync(ext_new, ext_old, (size_t)ncap * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    k_sort_perm<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, key, rank, bscan, ext_old, perm, ext_new);
+    k_permute<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, ncap, perm, state, state_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap, const int* perm,
+                             const float* src, float* dst, cudaStream_t st) {
+    if (n_chunks == 0) return cudaSuccess;
+    k_unpermute<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, ncap, perm, src, dst);
     return cudaGetLastError();
 }
 

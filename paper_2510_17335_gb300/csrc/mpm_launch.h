@@ -6,7 +6,7 @@
 
 namespace mpm {
 
-enum class KernelId : int { P2G = 0, Grid, G2P, G2PBwd, GridBwd, P2GBwd, GridClear, Count };
+enum class KernelId : int { P2G = 0, Grid, G2P, G2PBwd, GridBwd, P2GBwd, GridClear, SlotClear, Count };
 
 // one substep kernel; forward kernels read only A.f
 cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s);
@@ -16,6 +16,15 @@ cudaError_t launch_adj_from_ext(long long ncap, long long nslots, const int* ext
                                 const float* gv, float* adj, cudaStream_t st);
 cudaError_t launch_state_to_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* s, float* x,
                                 float* v, float* C, float* F, cudaStream_t st);
+// reorder the particles of every instance by cell (n_keys = cells of all
+// instances): state -> state_out, ext_old -> ext_new, perm[new] = old; 6 kernels
+cudaError_t launch_sort(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap, int n_keys,
+                        const float* state, float* state_out, const int* ext_old, int* ext_new, int* key, int* rank,
+                        int* bcount, int* bscan, int* part, int* perm, cudaStream_t st);
+constexpr int kSortLaunches = 6;
+// dst[perm[q]] = src[q] for all 24 components
+cudaError_t launch_unpermute(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap, const int* perm,
+                             const float* src, float* dst, cudaStream_t st);
 cudaError_t launch_grid_mass(const InstDev* inst, const int* block_inst, int n_blocks, const float4* vout,
                              double* mass, cudaStream_t st);
 cudaError_t launch_loss_mse(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap,

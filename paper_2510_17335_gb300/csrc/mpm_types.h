@@ -24,6 +24,7 @@ struct InstDev {
     int blk_off;            // first grid block of this instance
     long long pbeg;         // first particle slot
     long long node_off;     // first node (blocked layout)
+    long long ext_off;      // first particle in external order
     float dx, inv_dx, dt;
     float g[3];
     float mu, lam, alpha, beta;   // beta = (3 lam + 2 mu) / (2 mu) * alpha
@@ -53,6 +54,7 @@ struct StepArgs {
     int* status;
     unsigned long long* fp64_count;
     float clip;             // > 0: clip adjoints to [-clip, clip]
+    int tile;               // 1: sum scatters in a shared-memory tile per CTA
 };
 
 // Arguments of one substep's adjoint kernels.

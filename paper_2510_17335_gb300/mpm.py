@@ -47,7 +47,7 @@ class mpm_config(ctypes.Structure):
 
 class mpm_options(ctypes.Structure):
     _fields_ = [("checkpoint_every", ctypes.c_int), ("clip_grads", ctypes.c_int), ("clip_value", ctypes.c_double),
-                ("sigma_min", ctypes.c_double), ("sort_every", ctypes.c_int)]
+                ("sigma_min", ctypes.c_double), ("sort_every", ctypes.c_int), ("tile_scatter", ctypes.c_int)]
 
 
 class mpm_skill(ctypes.Structure):
@@ -151,10 +151,11 @@ def make_config(res, dx, dt, particle_volume, gravity=(0.0, -9.8, 0.0), bound=3,
     return c
 
 
-def make_options(checkpoint_every=50, clip_grads=0, clip_value=1e4, sigma_min=1e-4, sort_every=0) -> mpm_options:
+def make_options(checkpoint_every=50, clip_grads=0, clip_value=1e4, sigma_min=1e-4, sort_every=0,
+                 tile_scatter=0) -> mpm_options:
     o = mpm_options()
     o.checkpoint_every, o.clip_grads, o.clip_value = int(checkpoint_every), int(clip_grads), float(clip_value)
-    o.sigma_min, o.sort_every = float(sigma_min), int(sort_every)
+    o.sigma_min, o.sort_every, o.tile_scatter = float(sigma_min), int(sort_every), int(tile_scatter)
     return o
 
 
@@ -295,7 +296,7 @@ class Simulation:
     def profile_read(self) -> dict:
         """{kernel name: (total device ms, launches)} for every kernel."""
         out = {}
-        for k in range(7):
+        for k in range(8):
             ms = ctypes.c_double()
             n = ctypes.c_int64()
             check(lib().mpm_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)), "mpm_profile_read")

@@ -77,8 +77,16 @@ def _oracle_grad(w, state, nsub, seed, clip=0):
 
 
 def _seed(w, seed):
+    """Coherent loss seeds, like the MSE gradient 2 (x - xhat) / N of a target
+    shifted from the final state: a common direction plus 10% noise. (Pure
+    noise seeds make the parameter gradients sums that cancel ~100x, whose
+    value then hinges on the few particles that sit exactly on the yield
+    surface, where the FP32 and FP64 trajectories may take different
+    branches.)"""
     rng = np.random.default_rng(seed)
-    return rng.normal(size=(w.n, 3)) / w.n, rng.normal(size=(w.n, 3)) * 1e-3 / w.n
+    d = np.array([1.0, -0.5, 0.3])
+    return ((d + 0.1 * rng.normal(size=(w.n, 3))) / w.n,
+            (1e-3 * d + 1e-4 * rng.normal(size=(w.n, 3))) / w.n)
 
 
 def test_adjoint_matches_oracle_contact_scenario():
@@ -255,3 +263,29 @@ def test_full_size_adjoint_against_oracle():
     idx = rng.choice(w.n, 4096, replace=False)
     e = rel_err(gs["x"][idx], g["x"][idx])
     assert np.quantile(e, 0.99) < BAR
+
+
+def test_sorted_segments_give_the_same_gradients():
+    """Sorting the particles at every segment start (the backward undoes
+    each permutation on the adjoint) changes only the order of the float
+    sums: material gradients and state adjoints agree to 1e-4."""
+    w = _contact_workload()
+    rng = np.random.default_rng(31)
+    perm = rng.permutation(w.n)
+    w.x0 = w.x0[perm]
+    state = _strained_state(w, 14)
+    seed = _seed(w, 15)
+    res = []
+    for sort_every in (1, 0):
+        opts = mpm.make_options(checkpoint_every=4, sort_every=sort_every)
+        with mpm.simulation_from_workloads([w], opts) as sim:
+            sim.set_state(*state)
+            sim.forward(12, record=True)
+            gm, _ = sim.backward(dL_dx=seed[0].astype(np.float32), dL_dv=seed[1].astype(np.float32))
+            res.append((gm[0], sim.state_grad()))
+    assert rel_err(res[0][0], res[1][0]).max() < 1e-4
+    for k in ("x", "v", "F"):
+        a, b = res[0][1][k], res[1][1][k]
+        assert np.abs(a - b).max() <= 1e-4 * np.abs(b).max(), k
+    g, _, _ = _oracle_grad(w, state, 12, seed)
+    assert rel_err(res[0][0], g["material"]).max() < BAR
