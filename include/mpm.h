@@ -192,6 +192,35 @@ int mpm_profile(mpm_handle* h, int enable);
 int mpm_profile_read(mpm_handle* h, int kernel, double* total_ms, int64_t* launches);
 const char* mpm_kernel_name(int kernel);
 
+/* The MSE loss of mpm_loss_mse for one point set given as plain device
+ * arrays, for callers that cannot allocate device memory. (The paper has no
+ * counterpart of this entry point.)
+ *
+ * Who needs it: a caller whose device memory is all owned by another
+ * allocator (for example a framework's caching allocator that reserved the
+ * GPU up front), or a control loop that must not take the implicit device
+ * synchronisation of cudaMalloc. The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine. Its scratch is a file-scope device
+ * array of 128 KiB (plus a result and a counter) that every GPU which loads
+ * this library holds until the process exits.
+ *
+ * x, x_target: device pointers, n points of 3 floats (x[3*p + k]);
+ * dL_dx: device pointer for 2 (x - xhat) / n, or NULL; loss: host pointer,
+ * receives (1/n) sum_p |x_p - xhat_p|^2 accumulated in FP64. stream: a
+ * cudaStream_t (NULL = legacy default); the call waits for it before it
+ * returns. n must be in [0, MPM_NOALLOC_MAX_POINTS]; a larger n is rejected
+ * with MPM_ERR_INVALID_ARG before anything runs.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. All calls share the one scratch array, which
+ * keeps the last call's contents (the call clears the part that must start
+ * at zero), so calls that overlap on the GPU race with each other: issue
+ * them on one stream or one after another. */
+#define MPM_NOALLOC_MAX_POINTS 4194304
+int mpm_loss_mse_noalloc(const float* x, const float* x_target, int64_t n, float* dL_dx, double* loss,
+                         void* stream);
+
 /* Run on this CUDA stream (a cudaStream_t; NULL = the legacy default). */
 int mpm_set_stream(mpm_handle* h, void* stream);
 

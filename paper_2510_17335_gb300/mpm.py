@@ -87,6 +87,7 @@ EXPORTS = {
     "mpm_profile": (_ip, [_vp, _ip]),
     "mpm_profile_read": (_ip, [_vp, _ip, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "mpm_kernel_name": (ctypes.c_char_p, [_ip]),
+    "mpm_loss_mse_noalloc": (_ip, [_fp, _fp, ctypes.c_int64, _fp, _dp, _vp]),
     "mpm_destroy": (None, [_vp]),
     "mpm_error_string": (ctypes.c_char_p, [_ip]),
     "mpm_version": (_ip, []),
@@ -134,6 +135,18 @@ def _is_device(*arrays) -> bool:
         if a is not None and hasattr(a, "is_cuda"):
             return bool(a.is_cuda)
     return False
+
+
+def loss_mse_noalloc(x, target, dL_dx=None, stream_ptr: int = 0) -> float:
+    """mpm_loss_mse_noalloc on device tensors x, target [n, 3] (float32);
+    writes dL/dx into dL_dx if given; returns the loss."""
+    L = ctypes.c_double()
+    xp, _ = _ptr(x, True)
+    tp, _ = _ptr(target, True)
+    gp, _ = _ptr(dL_dx, True) if dL_dx is not None else (None, None)
+    check(lib().mpm_loss_mse_noalloc(xp, tp, int(x.shape[0]), gp, ctypes.byref(L), ctypes.c_void_p(stream_ptr)),
+          "mpm_loss_mse_noalloc")
+    return L.value
 
 
 def make_config(res, dx, dt, particle_volume, gravity=(0.0, -9.8, 0.0), bound=3, friction=0.5,
