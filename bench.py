@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="shared-memory tile scatter (1) or global atomics (0)")
-    ap.add_argument("--sort", type=int, default=0, help="sort particles by grid block every n substeps (0: never)")
+    ap.add_argument("--sort", type=int, default=0, help="sort particles by cell every n substeps (0: never)")
+    ap.add_argument("--batch", type=int, default=64, help="instances of the batched-vs-serial leg (0: skip)")
+    ap.add_argument("--batch-substeps", type=int, default=50)
     return ap.parse_args()
 
 
@@ -182,6 +184,54 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+# batched vs serial: uneven instances in one handle vs one handle each
+# --------------------------------------------------------------------------
+def batched_vs_serial(n_inst: int, nsub: int, steps: int, sort_every: int):
+    import numpy as np
+    import torch
+
+    from paper_2510_17335_gb300 import mpm
+    from paper_2510_17335_gb300 import workloads as W
+
+    ws = W.batch_uneven(n_inst, n_substeps=nsub)
+    K = max(1, nsub // 2)
+    opts = mpm.make_options(checkpoint_every=K, sort_every=sort_every)
+    n_total = sum(w.n for w in ws)
+
+    def run(sims, groups):
+        for sim, g in zip(sims, groups):
+            sim.reset()
+            sim.forward(nsub, record=True)
+            tgt = np.concatenate([w.x0 for w in g]) + np.float32(0.002)
+            _, dl = sim.loss_mse(tgt)
+            sim.backward(dL_dx=dl)
+
+    def timed(sims, groups):
+        run(sims, groups)                      # warm-up (allocations)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            run(sims, groups)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / steps
+
+    sim = mpm.simulation_from_workloads(ws, opts)
+    tb = timed([sim], [ws])
+    launches_b = sim.info()["kernel_launches"]
+    sim.close()
+    sims = [mpm.simulation_from_workloads([w], opts) for w in ws]
+    ts = timed(sims, [[w] for w in ws])
+    for s_ in sims:
+        s_.close()
+    return {"instances": n_inst, "particles_total": n_total, "particles_min": min(w.n for w in ws),
+            "particles_max": max(w.n for w in ws), "grids": f"{min(w.res[0] for w in ws)}^3-{max(w.res[0] for w in ws)}^3",
+            "substeps": nsub, "checkpoint_every": K,
+            "batched_particle_substeps_per_s": n_total * nsub / tb,
+            "serial_particle_substeps_per_s": n_total * nsub / ts, "speedup": ts / tb,
+            "batched_s_per_step": tb, "serial_s_per_step": ts}
+
+
+# --------------------------------------------------------------------------
 # our implementation
 # --------------------------------------------------------------------------
 def run_ours(args):
@@ -243,7 +293,6 @@ def run_ours(args):
             fwd_step()
         # ---- timed: forward + backward ----
         launches0 = sim.info()["kernel_launches"]
-        sim.profile(True)
         clocks = ClockSampler(bus)
         clocks.start()
         barrier()
@@ -256,10 +305,17 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         clk = clocks.stop()
-        prof = sim.profile_read()
-        sim.profile(False)
         launches = sim.info()["kernel_launches"] - launches0
         ms = e0.elapsed_time(e1)
+        # ---- the same steps again with a CUDA event pair around every kernel
+        # (on the library's stream) for the per-kernel times and the roofline;
+        # kept out of the timed region above, which the events slow by ~4% ----
+        sim.profile(True)
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        prof = sim.profile_read()
+        sim.profile(False)
         # ---- forward only ----
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -330,18 +386,19 @@ def run_ours(args):
         algo = ALGO_BYTES[name] * N
         ach = algo / avg_s / 1e9
         traffic = None
-        tf = os.path.join(ROOT, "profiles", "dram_traffic.json")
+        tf = os.path.join(ROOT, "profiles", "dram_traffic.txt")
         if os.path.exists(tf):
-            try:
-                d = json.load(open(tf))
-                ent = d.get(name)
-                if ent and ent.get("kernel_source_sha") == kernel_source_sha():
-                    traffic = ent["dram_bytes_per_launch_full_size"]
-            except Exception:
-                traffic = None
+            for line in open(tf):
+                f = line.split()
+                if len(f) >= 3 and not line.startswith("#") and f[0] == name and f[1] == kernel_source_sha():
+                    traffic = int(f[2])
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                 "traffic": traffic, "kernel": name, "algo_bytes_per_launch": algo,
-                "avg_launch_us": round(avg_s * 1e6, 2), "peak_kind": f"{peak_kind} hbm_gbs"}
+                "avg_launch_us": round(avg_s * 1e6, 2), "peak_kind": f"{peak_kind} hbm_gbs",
+                "timing": "CUDA events around every launch, repetition of the timed steps"}
+    batch = None
+    if args.batch > 0:
+        batch = batched_vs_serial(args.batch, args.batch_substeps, 2, args.sort)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         r, secs, desc = oracle_sample(w, 24, 16, args.start)
@@ -358,6 +415,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}"},
         "fwd_value": fwd_value, "fwd_ms_per_step": fms / args.steps,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "batched_vs_serial": batch,
         "kernels": kernels, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

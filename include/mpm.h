@@ -179,6 +179,15 @@ int mpm_get_action_grad(mpm_handle* h, int inst, double* dL_dactions, double* dL
  * (Sec. III-A, MLS-MPM transfer) it equals sum_p rho V_p up to rounding. */
 int mpm_grid_mass(mpm_handle* h, double* mass);
 
+/* Autotuner: from the current state, time a recorded forward of
+ * trial_substeps plus its backward (CUDA events) for each candidate of
+ * {global-atomic or shared-tile scatter} x {no sort, sort by cell}; keep the
+ * fastest as the handle's tile_scatter and sort_every (sorting then happens
+ * once per checkpoint segment) and write them to chosen[2] (may be NULL).
+ * The state, the substep counter and the options not tuned are restored;
+ * any record is dropped. */
+int mpm_autotune(mpm_handle* h, int trial_substeps, int* chosen);
+
 /* Set the substep counter (the index into the shovel pose tables) of the
  * next forward substep; drops any record. */
 int mpm_set_substep(mpm_handle* h, int64_t substep);
@@ -186,8 +195,13 @@ int mpm_set_substep(mpm_handle* h, int64_t substep);
 /* Kernel timing: enable != 0 records a CUDA event pair around every kernel
  * launch on the handle's stream (counters reset on every call). Kernel ids:
  * 0 k_p2g, 1 k_grid, 2 k_g2p, 3 k_g2p_bwd, 4 k_grid_bwd, 5 k_p2g_bwd,
- * 6 k_grid_clear, 7 k_slot_clear. mpm_profile_read waits for the recorded events and gives
- * the summed device time (ms) and the launch count of one kernel. */
+ * 6 k_grid_clear, 7 k_slot_clear, 8 k_p2g_fp64, 9 k_p2g_bwd_fp64 (ids below
+ * MPM_PROFILE_KERNELS). The two _fp64 kernels redo, in FP64, the particles
+ * whose deformation gradient is too ill-conditioned for the FP32 SVD; they
+ * launch every substep and return at once when there are none.
+ * mpm_profile_read waits for the recorded events and gives the summed device
+ * time (ms) and the launch count of one kernel. */
+#define MPM_PROFILE_KERNELS 10
 int mpm_profile(mpm_handle* h, int enable);
 int mpm_profile_read(mpm_handle* h, int kernel, double* total_ms, int64_t* launches);
 const char* mpm_kernel_name(int kernel);

@@ -146,6 +146,7 @@ struct mpm_handle {
     DevBuf<unsigned char> d_flags;
     DevBuf<int> d_status;
     DevBuf<unsigned long long> d_fp64;
+    DevBuf<int> d_fb_list, d_fb_count;   // particles deferred to the FP64 kernels
     DevBuf<double> d_loss;
 
     // record / backward
@@ -384,6 +385,8 @@ StepArgs base_args(mpm_handle* h) {
     a.n_blocks = h->n_blocks;
     a.status = h->d_status.p;
     a.fp64_count = h->d_fp64.p;
+    a.fb_list = h->d_fb_list.p;
+    a.fb_count = h->d_fb_count.p;
     a.clip = h->opt.clip_grads ? (float)h->opt.clip_value : 0.0f;
     a.tile = h->tile_scatter;
     return a;
@@ -435,6 +438,7 @@ int run_substep(mpm_handle* h, const StepArgs& a) {
     std::memset(&A, 0, sizeof A);
     A.f = a;
     RK(run_kernel(h, KernelId::P2G, A));
+    RK(run_kernel(h, KernelId::P2GFp64, A));
     RK(run_kernel(h, KernelId::Grid, A));
     RK(run_kernel(h, KernelId::G2P, A));
     return MPM_OK;
@@ -523,6 +527,7 @@ int run_adjoint_substep(mpm_handle* h, const AdjArgs& A) {
     RK(run_kernel(h, KernelId::G2PBwd, A));
     RK(run_kernel(h, KernelId::GridBwd, A));
     RK(run_kernel(h, KernelId::P2GBwd, A));
+    RK(run_kernel(h, KernelId::P2GBwdFp64, A));
     RK(run_kernel(h, KernelId::GridClear, A));
     return MPM_OK;
 }
@@ -636,7 +641,9 @@ int mpm_create(int n_inst, const mpm_config* cfgs, const mpm_material* mats, con
         (rc = h->d_x0.ensure((size_t)std::max<int64_t>(n_ext, 1) * 3, h->device_bytes)) ||
         (rc = h->d_acc.ensure(node, h->device_bytes)) || (rc = h->d_vout.ensure(node, h->device_bytes)) ||
         (rc = h->d_flags.ensure(blk, h->device_bytes)) || (rc = h->d_status.ensure(1, h->device_bytes)) ||
-        (rc = h->d_fp64.ensure(1, h->device_bytes)) || (rc = h->d_loss.ensure(n_inst, h->device_bytes)))
+        (rc = h->d_fp64.ensure(1, h->device_bytes)) || (rc = h->d_loss.ensure(n_inst, h->device_bytes)) ||
+        (rc = h->d_fb_list.ensure(std::max<int64_t>(h->ncap, 1), h->device_bytes)) ||
+        (rc = h->d_fb_count.ensure(2, h->device_bytes)))
         return fail(rc);
     std::vector<int> ci(std::max(chunks, 1), 0), bi(blk), eos(h->ncap, -1);
     for (int i = 0; i < n_inst; i++) {
@@ -654,7 +661,7 @@ int mpm_create(int n_inst, const mpm_config* cfgs, const mpm_material* mats, con
         cudaMemsetAsync(h->d_vout.p, 0, node * sizeof(float4), s) || cudaMemsetAsync(h->d_flags.p, 0, blk, s) ||
         cudaMemsetAsync(h->d_status.p, 0, sizeof(int), s) ||
         cudaMemsetAsync(h->d_fp64.p, 0, sizeof(unsigned long long), s) ||
-        cudaStreamSynchronize(s)) {
+        cudaMemsetAsync(h->d_fb_count.p, 0, 2 * sizeof(int), s) || cudaStreamSynchronize(s)) {
         cudaGetLastError();
         return fail(MPM_ERR_CUDA);
     }
@@ -671,7 +678,7 @@ void mpm_destroy(mpm_handle* h) {
     h->d_inst.release(); h->d_chunk_inst.release(); h->d_block_inst.release(); h->d_ext_of_slot.release();
     h->d_state.release(); h->d_x0.release(); h->d_stage.release(); h->d_poses.release(); h->d_target.release();
     h->d_acc.release(); h->d_vout.release(); h->d_flags.release(); h->d_status.release(); h->d_fp64.release();
-    h->d_loss.release();
+    h->d_loss.release(); h->d_fb_list.release(); h->d_fb_count.release();
     for (auto& c : h->ckpt) c.release();
     for (auto& b : h->seg_state) b.release();
     for (auto& b : h->seg_acc) b.release();
@@ -1103,6 +1110,83 @@ int mpm_get_action_grad(mpm_handle* h, int inst, double* dL_dactions, double* dL
     return MPM_OK;
 }
 
+int mpm_autotune(mpm_handle* h, int trial_substeps, int* chosen) {
+    if (!h || trial_substeps < 1 || trial_substeps > 100000) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    // the state and substep this call starts from are restored afterwards
+    const size_t state_floats = (size_t)h->ncap * kStateComps;
+    DevBuf<float> save;
+    DevBuf<int> save_ext;
+    RK(save.ensure(state_floats, h->device_bytes));
+    RK(save_ext.ensure((size_t)h->ncap, h->device_bytes));
+    CK(cudaMemcpyAsync(save.p, h->d_state.p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(save_ext.p, h->d_ext_of_slot.p, (size_t)h->ncap * sizeof(int), cudaMemcpyDeviceToDevice,
+                       h->stream));
+    const int64_t substep0 = h->substep;
+    const mpm_options opt0 = h->opt;
+    struct Cand {
+        int tile, sort;
+    };
+    const Cand cands[4] = {{0, 0}, {1, 0}, {0, trial_substeps}, {1, trial_substeps}};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_i = 0, rc = MPM_OK;
+    for (int c = 0; c < 4 && rc == MPM_OK; c++) {
+        for (int rep = 0; rep < 2 && rc == MPM_OK; rep++) {   // the first run allocates
+            CK(cudaMemcpyAsync(h->d_state.p, save.p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice,
+                               h->stream));
+            CK(cudaMemcpyAsync(h->d_ext_of_slot.p, save_ext.p, (size_t)h->ncap * sizeof(int),
+                               cudaMemcpyDeviceToDevice, h->stream));
+            h->substep = substep0;
+            h->recording = false;
+            h->seg_valid = -1;
+            h->tile_scatter = cands[c].tile;
+            h->opt.sort_every = cands[c].sort;
+            h->since_sort = 1LL << 40;
+            CK(cudaEventRecord(e0, h->stream));
+            rc = mpm_forward(h, trial_substeps, 1);
+            if (rc == MPM_OK) rc = mpm_backward(h, nullptr, nullptr, 1, nullptr, nullptr);
+            CK(cudaEventRecord(e1, h->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep == 1 && ms < best) {
+                best = ms;
+                best_i = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaMemcpyAsync(h->d_state.p, save.p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_ext_of_slot.p, save_ext.p, (size_t)h->ncap * sizeof(int), cudaMemcpyDeviceToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->device_bytes -= (int64_t)(save.n * sizeof(float) + save_ext.n * sizeof(int));
+    save.release();
+    save_ext.release();
+    h->substep = substep0;
+    h->recording = false;
+    h->seg_valid = -1;
+    h->have_grad = false;
+    h->opt = opt0;
+    if (rc != MPM_OK) {
+        h->tile_scatter = opt0.tile_scatter ? 1 : 0;
+        return rc;
+    }
+    h->tile_scatter = cands[best_i].tile;
+    h->opt.tile_scatter = cands[best_i].tile;
+    h->opt.sort_every = cands[best_i].sort ? std::max(h->opt.checkpoint_every, 1) : 0;
+    h->since_sort = 1LL << 40;
+    if (chosen) {
+        chosen[0] = h->opt.tile_scatter;
+        chosen[1] = h->opt.sort_every;
+    }
+    return MPM_OK;
+}
+
 int mpm_set_substep(mpm_handle* h, int64_t substep) {
     if (!h || substep < 0 || substep > (1LL << 30)) return MPM_ERR_INVALID_ARG;
     h->substep = substep;
@@ -1131,7 +1215,8 @@ int mpm_profile_read(mpm_handle* h, int kernel, double* total_ms, int64_t* launc
 
 const char* mpm_kernel_name(int kernel) {
     static const char* names[] = {"k_p2g",     "k_grid",       "k_g2p",       "k_g2p_bwd",
-                                  "k_grid_bwd", "k_p2g_bwd", "k_grid_clear", "k_slot_clear"};
+                                  "k_grid_bwd", "k_p2g_bwd", "k_grid_clear", "k_slot_clear",
+                                  "k_p2g_fp64", "k_p2g_bwd_fp64"};
     if (kernel < 0 || kernel >= (int)KernelId::Count) return "";
     return names[kernel];
 }

@@ -167,14 +167,13 @@ MPM_HD __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3], T 
     T sj = dsqrt<T>(uj[0] * uj[0] + uj[1] * uj[1] + uj[2] * uj[2]);
     if (!(sj > T(1e-30) * si)) {
         // rank one: any unit vector orthogonal to u_i
+        // (static indices only: a runtime index would put the caller's arrays in local memory)
         int a = 0;
-        if (fabs(ui[1]) < fabs(ui[a])) a = 1;
-        if (fabs(ui[2]) < fabs(ui[a])) a = 2;
-        T e[3] = {T(0), T(0), T(0)};
-        e[a] = T(1);
-        const T d = ui[a];
+        if (fabs(ui[1]) < fabs(ui[0])) a = 1;
+        if (fabs(ui[2]) < fabs(a == 0 ? ui[0] : ui[1])) a = 2;
+        const T d = a == 0 ? ui[0] : (a == 1 ? ui[1] : ui[2]);
 #pragma unroll
-        for (int r = 0; r < 3; r++) uj[r] = e[r] - d * ui[r];
+        for (int r = 0; r < 3; r++) uj[r] = (r == a ? T(1) : T(0)) - d * ui[r];
         const T ne = dsqrt<T>(uj[0] * uj[0] + uj[1] * uj[1] + uj[2] * uj[2]);
 #pragma unroll
         for (int r = 0; r < 3; r++) uj[r] /= ne;
@@ -200,9 +199,8 @@ MPM_HD __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3], T 
         U[r][1] = c1;
         U[r][2] = c2;
     }
-    s[i] = si;
-    s[j] = sj;
-    s[m] = sm;
+#pragma unroll
+    for (int k = 0; k < 3; k++) s[k] = (k == i) ? si : ((k == j) ? sj : sm);
     h[0] = l0;
     h[1] = l1;
     h[2] = l2;

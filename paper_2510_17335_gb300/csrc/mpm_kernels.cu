@@ -1,23 +1,85 @@
 // Kernels of the MLS-MPM sand substep (Algorithm 1 of DDBot, arXiv
 // 2510.17335) and of its adjoint, for sm_103a.
 //
-// Forward substep (3 launches, all instances of a batch in each):
-//   k_p2g   particle: trial F, SVD, Drucker-Prager return, Kirchhoff stress,
-//           APIC scatter of (m, mv) into the blocked grid; marks grid blocks
-//   k_grid  grid block (one warp): v = mv/m + dt g, walls, shovel contact
-//   k_g2p   particle: APIC gather of v and C, particle contact, advection
-// Adjoint substep (4 launches): k_g2p_bwd (scatter into the grid adjoint),
-// k_grid_bwd, k_p2g_bwd (gather, constitutive adjoint, parameter sums),
-// k_grid_clear.
+// Forward substep (4 launches, all instances of a batch in each):
+//   k_p2g       particle: trial F, SVD, Drucker-Prager return, Kirchhoff
+//               stress, APIC scatter of (m, mv) into the blocked grid; marks
+//               grid blocks. Particles whose F is ill-conditioned for FP32
+//               go to a list instead.
+//   k_p2g_fp64  the listed particles with the constitutive step in FP64
+//   k_grid      grid block (one warp): v = mv/m + dt g, walls, shovel contact
+//   k_g2p       particle: APIC gather of v and C, particle contact, advection
+// Adjoint substep (5 launches): k_g2p_bwd (scatter into the grid adjoint),
+// k_grid_bwd, k_p2g_bwd (gather, constitutive adjoint, parameter sums; the
+// same deferral), k_p2g_bwd_fp64, k_grid_clear.
+//
+// The FP64 code lives only in the two fix-up kernels, so that the register
+// budget of the main particle kernels is set by the FP32 path.
 #include <cuda_runtime.h>
 
 #include "mpm_device.cuh"
 #include "mpm_launch.h"
 
+// minimum resident CTAs per SM of the particle kernels (register caps)
+#ifndef MPM_MINB_P2G
+#define MPM_MINB_P2G 3
+#endif
+#ifndef MPM_MINB_G2P
+#define MPM_MINB_G2P 4
+#endif
+#ifndef MPM_MINB_G2P_BWD
+#define MPM_MINB_G2P_BWD 3
+#endif
+#ifndef MPM_MARK_COND
+#define MPM_MARK_COND 1
+#endif
+#ifndef MPM_MINB_P2G_BWD
+#define MPM_MINB_P2G_BWD 2
+#endif
+
 namespace mpm {
 
 __device__ __forceinline__ float ld(const float* s, long long ncap, int comp, long long p) {
     return s[comp * ncap + p];
+}
+
+// a[i] through selects: the stencil loops over i stay rolled (code size),
+// and a runtime index would move the whole stencil into local memory
+template <typename T>
+__device__ __forceinline__ T sel3(const T (&a)[3], int i) {
+    return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]);
+}
+
+// The x-axis weights, weight derivatives and node offsets of a stencil as a
+// small array that the rolled loop over i indexes at run time (it lives in
+// local memory; the rest of the stencil stays in registers).
+struct AxisX {
+    float w[3], dw[3];
+    int o[3];
+};
+
+__device__ __forceinline__ AxisX axis_x(const Stencil& st, const int (&ox)[3]) {
+    AxisX l;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        l.w[i] = st.w[0][i];
+        l.dw[i] = st.dw[0][i];
+        l.o[i] = ox[i];
+    }
+    return l;
+}
+
+// Copy the CTA's instance record into shared memory (all threads call it).
+// Reads of its fields are then shared-memory loads; from global memory the
+// compiler would have to reload them after every store of the kernel.
+__device__ __forceinline__ const InstDev& stage_instance(InstDev& sI, const InstDev* inst, int i) {
+    static_assert(sizeof(InstDev) % 4 == 0, "InstDev is copied as 32-bit words");
+    constexpr int W = sizeof(InstDev) / 4;
+    const int* src = reinterpret_cast<const int*>(inst + i);
+    int* dst = reinterpret_cast<int*>(&sI);
+    for (int k = threadIdx.x; k < W; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    return sI;
 }
 
 // mark the (up to 8) grid blocks a stencil touches
@@ -28,18 +90,97 @@ __device__ __forceinline__ void mark_blocks(const InstDev& I, const Stencil& st,
     for (int bx = b0x; bx <= b1x; bx++)
         for (int by = b0y; by <= b1y; by++)
             for (int bz = b0z; bz <= b1z; bz++) {
+#if MPM_MARK_COND
+            {
                 unsigned char* f = flags + I.blk_off + (bx * I.nb[1] + by) * I.nb[2] + bz;
                 if (*f == 0) *f = 1;
+            }
+#else
+                flags[I.blk_off + (bx * I.nb[1] + by) * I.nb[2] + bz] = 1;
+#endif
             }
 }
 
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kChunk, 3) k_p2g(StepArgs a) {
+__device__ __forceinline__ void load_trial(const InstDev& I, const StepArgs& a, long long p, float (&C)[3][3],
+                                           float (&Ft)[3][3]) {
+    const long long N = a.ncap;
+    float F[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            C[r][c] = ld(a.sin, N, kC + 3 * r + c, p);
+            F[r][c] = ld(a.sin, N, kF + 3 * r + c, p);
+        }
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            Ft[r][c] = F[r][c] + I.dt * (C[r][0] * F[0][c] + C[r][1] * F[1][c] + C[r][2] * F[2][c]);
+}
+
+// APIC + MLS stress transfer of one particle to its 27 nodes: mass m_p W and
+// momentum W (m_p v + A d), A = stress_scale tau + m_p C. Sums in the shared
+// tile when T is given and tiled, else with global atomics.
+__device__ __forceinline__ void p2g_scatter(TileSmem* T, const InstDev& I, float4* grid, const Stencil& st,
+                                            const float (&v)[3], const float (&A)[3][3]) {
+    int ox[3], oy[3], oz[3];
+    node_offsets(I, st, ox, oy, oz);
+    float mv[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) mv[k] = I.mp * v[k];
+    float4* acc = grid + I.node_off;
+#pragma unroll 1
+    for (int i = 0; i < 3; i++) {
+        const float dxi = (float(i) - st.fx[0]) * I.dx;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float dyj = (float(j) - st.fx[1]) * I.dx;
+            const float wij = sel3(st.w[0], i) * st.w[1][j];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float dzk = (float(k) - st.fx[2]) * I.dx;
+                const float W = wij * st.w[2][k];
+                float4 val;
+                val.x = W * I.mp;
+                val.y = W * (mv[0] + A[0][0] * dxi + A[0][1] * dyj + A[0][2] * dzk);
+                val.z = W * (mv[1] + A[1][0] * dxi + A[1][1] * dyj + A[1][2] * dzk);
+                val.w = W * (mv[2] + A[2][0] * dxi + A[2][1] * dyj + A[2][2] * dzk);
+                if (T) tile_add(*T, acc, sel3(ox, i) + oy[j] + oz[k], st, i, j, k, val, 4);
+                else atomicAdd(acc + sel3(ox, i) + oy[j] + oz[k], val);
+            }
+        }
+    }
+}
+
+// stores F' = Fn and the affine matrix of the transfer
+__device__ __forceinline__ void p2g_store_affine(const InstDev& I, const StepArgs& a, long long p,
+                                                 const float (&Fn)[3][3], const float (&tau)[3][3],
+                                                 const float (&C)[3][3], float (&A)[3][3]) {
+    const long long N = a.ncap;
+    bool finite = true;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            a.sout[(kF + 3 * r + c) * N + p] = Fn[r][c];
+            finite = finite && isfinite(Fn[r][c]);
+            A[r][c] = I.stress_scale * tau[r][c] + I.mp * C[r][c];
+        }
+    if (!finite) atomicOr(a.status, kStatusNonFinite);
+}
+
+// P2G with the constitutive step, FP32. A particle whose deformation is
+// ill-conditioned for FP32 (see needs_fp64) is listed for k_p2g_fp64, which
+// does its constitutive step and transfer.
+__global__ void __launch_bounds__(kChunk, MPM_MINB_P2G) k_p2g(StepArgs a) {
     __shared__ TileSmem T;
+    __shared__ InstDev sI;
     const int inst = a.chunk_inst[blockIdx.x];
-    const InstDev& I = a.inst[inst];
+    const InstDev& I = stage_instance(sI, a.inst, inst);
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
     const bool active = p - I.pbeg < I.n;
     const long long N = a.ncap;
@@ -55,69 +196,70 @@ __global__ void __launch_bounds__(kChunk, 3) k_p2g(StepArgs a) {
     else if (threadIdx.x == 0) T.tiled = 0;
     if (!a.tile) __syncthreads();
     if (active) {
-        float v[3], C[3][3], F[3][3];
+        float v[3], C[3][3], Ft[3][3];
 #pragma unroll
         for (int k = 0; k < 3; k++) v[k] = ld(a.sin, N, kV + k, p);
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                C[r][c] = ld(a.sin, N, kC + 3 * r + c, p);
-                F[r][c] = ld(a.sin, N, kF + 3 * r + c, p);
-            }
-        // trial deformation gradient (I + dt C) F
-        float Ft[3][3];
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-                Ft[r][c] = F[r][c] + I.dt * (C[r][0] * F[0][c] + C[r][1] * F[1][c] + C[r][2] * F[2][c]);
-        float Fn[3][3], tau[3][3];
-        if (constitutive(Ft, I.mu, I.lam, I.beta, I.smin, Fn, tau)) atomicAdd(a.fp64_count, 1ull);
-        bool finite = true;
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                a.sout[(kF + 3 * r + c) * N + p] = Fn[r][c];
-                finite = finite && isfinite(Fn[r][c]);
-            }
-        if (!finite) atomicOr(a.status, kStatusNonFinite);
-        // affine momentum: stress term of MLS-MPM plus APIC
-        float A[3][3];
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) A[r][c] = I.stress_scale * tau[r][c] + I.mp * C[r][c];
-        int ox[3], oy[3], oz[3];
-        node_offsets(I, st, ox, oy, oz);
-        float mv[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++) mv[k] = I.mp * v[k];
-        float4* acc = a.acc + I.node_off;
-#pragma unroll 1
-        for (int i = 0; i < 3; i++) {
-            const float dxi = (float(i) - st.fx[0]) * I.dx;
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                const float dyj = (float(j) - st.fx[1]) * I.dx;
-                const float wij = st.w[0][i] * st.w[1][j];
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    const float dzk = (float(k) - st.fx[2]) * I.dx;
-                    const float W = wij * st.w[2][k];
-                    float4 val;
-                    val.x = W * I.mp;
-                    val.y = W * (mv[0] + A[0][0] * dxi + A[0][1] * dyj + A[0][2] * dzk);
-                    val.z = W * (mv[1] + A[1][0] * dxi + A[1][1] * dyj + A[1][2] * dzk);
-                    val.w = W * (mv[2] + A[2][0] * dxi + A[2][1] * dyj + A[2][2] * dzk);
-                    tile_add(T, acc, ox[i] + oy[j] + oz[k], st, i, j, k, val, 4);
-                }
-            }
+        load_trial(I, a, p, C, Ft);
+        Spectral<float> S;
+        constitutive_spectral<float>(Ft, I.mu, I.lam, I.beta, I.smin, S);
+        if (needs_fp64(S)) {
+            a.fb_list[atomicAdd(a.fb_count, 1)] = (int)p;
+        } else {
+            float Fn[3][3], tau[3][3], A[3][3];
+            spectral_outputs<float, float>(S, Fn, tau);
+            p2g_store_affine(I, a, p, Fn, tau, C, A);
+            p2g_scatter(&T, I, a.acc, st, v, A);
+            if (!T.tiled) mark_blocks(I, st, a.flags);
         }
-        if (!T.tiled) mark_blocks(I, st, a.flags);
     }
     tile_flush(T, I, a.acc, a.flags, kChunk);
+}
+
+// Deferred-list bookkeeping of the FP64 fix-up kernels: every CTA reads the
+// count, and the last CTA to finish zeroes the count and the ticket for the
+// next launch (stream order keeps the next producer behind it).
+__device__ __forceinline__ int fb_begin(const int* fb_count, int* scount) {
+    if (threadIdx.x == 0) *scount = *(volatile const int*)fb_count;
+    __syncthreads();
+    return *scount;
+}
+
+__device__ __forceinline__ void fb_end(int* fb_count) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(fb_count + 1, 1) == (int)gridDim.x - 1) {
+            fb_count[0] = 0;
+            fb_count[1] = 0;
+        }
+    }
+}
+
+// The particles k_p2g listed: constitutive step in FP64, transfer with
+// global atomics.
+__global__ void __launch_bounds__(kFp64Threads) k_p2g_fp64(StepArgs a) {
+    __shared__ int scount;
+    const int count = fb_begin(a.fb_count, &scount);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const long long p = a.fb_list[i];
+        const InstDev& I = a.inst[a.chunk_inst[p / kChunk]];
+        const long long N = a.ncap;
+        float x[3], v[3], C[3][3], Ft[3][3], Fn[3][3], tau[3][3], A[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            x[k] = ld(a.sin, N, kX + k, p);
+            v[k] = ld(a.sin, N, kV + k, p);
+        }
+        Stencil st;
+        make_stencil(I, x, st);
+        load_trial(I, a, p, C, Ft);
+        constitutive_fp64(Ft, I.mu, I.lam, I.beta, I.smin, Fn, tau);
+        p2g_store_affine(I, a, p, Fn, tau, C, A);
+        p2g_scatter(nullptr, I, a.acc, st, v, A);
+        mark_blocks(I, st, a.flags);
+        atomicAdd(a.fp64_count, 1ull);
+    }
+    fb_end(a.fb_count);
 }
 
 // velocity update of one node (gravity, walls); returns false for empty nodes
@@ -169,9 +311,10 @@ __global__ void __launch_bounds__(256) k_grid(StepArgs a) {
     if (!a.keep_grid && lane == 0) a.flags[gw] = 0;
 }
 
-__global__ void __launch_bounds__(kChunk, 4) k_g2p(StepArgs a) {
+__global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
+    __shared__ InstDev sI;
     const int inst = a.chunk_inst[blockIdx.x];
-    const InstDev& I = a.inst[inst];
+    const InstDev& I = stage_instance(sI, a.inst, inst);
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
     if (p - I.pbeg >= I.n) return;
     const long long N = a.ncap;
@@ -190,12 +333,12 @@ __global__ void __launch_bounds__(kChunk, 4) k_g2p(StepArgs a) {
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             const float dj = float(j) - st.fx[1];
-            const float wij = st.w[0][i] * st.w[1][j];
+            const float wij = sel3(st.w[0], i) * st.w[1][j];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 const float dk = float(k) - st.fx[2];
                 const float W = wij * st.w[2][k];
-                const float4 g = __ldg(vg + ox[i] + oy[j] + oz[k]);
+                const float4 g = __ldg(vg + sel3(ox, i) + oy[j] + oz[k]);
                 v[0] += W * g.x;
                 v[1] += W * g.y;
                 v[2] += W * g.z;
@@ -242,12 +385,13 @@ __global__ void __launch_bounds__(kChunk, 4) k_g2p(StepArgs a) {
 // ---------------------------------------------------------------------------
 // adjoint
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kChunk, 3) k_g2p_bwd(AdjArgs A) {
+__global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A) {
     __shared__ double sred[8 * 32];
     __shared__ TileSmem T;
+    __shared__ InstDev sI;
     const StepArgs& a = A.f;
     const int inst = a.chunk_inst[blockIdx.x];
-    const InstDev& I = a.inst[inst];
+    const InstDev& I = stage_instance(sI, a.inst, inst);
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
     const bool active = p - I.pbeg < I.n;
     const long long N = a.ncap;
@@ -290,8 +434,8 @@ __global__ void __launch_bounds__(kChunk, 3) k_g2p_bwd(AdjArgs A) {
                 for (int j = 0; j < 3; j++)
 #pragma unroll
                     for (int k = 0; k < 3; k++) {
-                        const float W = st.w[0][i] * st.w[1][j] * st.w[2][k];
-                        const float4 g = __ldg(vg + ox[i] + oy[j] + oz[k]);
+                        const float W = sel3(st.w[0], i) * st.w[1][j] * st.w[2][k];
+                        const float4 g = __ldg(vg + sel3(ox, i) + oy[j] + oz[k]);
                         v[0] += W * g.x; v[1] += W * g.y; v[2] += W * g.z;
                     }
             const Pose P = load_pose(I, a.substep);
@@ -305,18 +449,19 @@ __global__ void __launch_bounds__(kChunk, 3) k_g2p_bwd(AdjArgs A) {
         // adjoint of the APIC gather: scatter into the grid velocity adjoint
         const float kap = 4.0f * I.inv_dx * I.inv_dx;
         float4* ga = A.gacc + I.node_off;
+        const AxisX lx = axis_x(st, ox);
 #pragma unroll 1
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++)
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
-                    const float wx = st.w[0][i], wy = st.w[1][j], wz = st.w[2][k];
+                    const float wx = lx.w[i], wy = st.w[1][j], wz = st.w[2][k];
                     const float W = wx * wy * wz;
-                    const float gW[3] = {st.dw[0][i] * wy * wz, wx * st.dw[1][j] * wz, wx * wy * st.dw[2][k]};
+                    const float gW[3] = {lx.dw[i] * wy * wz, wx * st.dw[1][j] * wz, wx * wy * st.dw[2][k]};
                     const float d[3] = {(float(i) - st.fx[0]) * I.dx, (float(j) - st.fx[1]) * I.dx,
                                         (float(k) - st.fx[2]) * I.dx};
-                    const float4 g = __ldg(vg + ox[i] + oy[j] + oz[k]);
+                    const float4 g = __ldg(vg + lx.o[i] + oy[j] + oz[k]);
                     const float vi[3] = {g.x, g.y, g.z};
                     float Cd[3];
 #pragma unroll
@@ -326,7 +471,7 @@ __global__ void __launch_bounds__(kChunk, 3) k_g2p_bwd(AdjArgs A) {
                     contrib.y = W * (gvn[1] + kap * Cd[1]);
                     contrib.z = W * (gvn[2] + kap * Cd[2]);
                     contrib.w = 0.f;
-                    tile_add(T, ga, ox[i] + oy[j] + oz[k], st, i, j, k, contrib, 3);
+                    tile_add(T, ga, lx.o[i] + oy[j] + oz[k], st, i, j, k, contrib, 3);
                     const float Wbar = vi[0] * (gvn[0] + kap * Cd[0]) + vi[1] * (gvn[1] + kap * Cd[1]) +
                                        vi[2] * (gvn[2] + kap * Cd[2]);
 #pragma unroll
@@ -411,131 +556,275 @@ __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
     }
 }
 
-__global__ void __launch_bounds__(kChunk) k_p2g_bwd(AdjArgs A) {
+// spectral data parked in shared memory across the gather (37 words a thread)
+constexpr int kParked = 37;
+
+__device__ __forceinline__ void park(volatile float* sS, const Spectral<float>& S) {
+    const int t = threadIdx.x;
+    int w = 0;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            sS[(w++) * kChunk + t] = S.U[a][b];
+            sS[(w++) * kChunk + t] = S.V[a][b];
+        }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        sS[(w++) * kChunk + t] = S.s[k];
+        sS[(w++) * kChunk + t] = S.eps[k];
+        sS[(w++) * kChunk + t] = S.shat[k];
+        sS[(w++) * kChunk + t] = S.e[k];
+        sS[(w++) * kChunk + t] = S.t[k];
+    }
+    sS[(w++) * kChunk + t] = S.nh;
+    sS[(w++) * kChunk + t] = S.tr;
+    sS[(w++) * kChunk + t] = S.kappa;
+    sS[(w++) * kChunk + t] = __int_as_float(S.kase);
+}
+
+__device__ __forceinline__ void unpark(const volatile float* sS, Spectral<float>& S, float smin) {
+    const int t = threadIdx.x;
+    int w = 0;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            S.U[a][b] = sS[(w++) * kChunk + t];
+            S.V[a][b] = sS[(w++) * kChunk + t];
+        }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        S.s[k] = sS[(w++) * kChunk + t];
+        S.eps[k] = sS[(w++) * kChunk + t];
+        S.shat[k] = sS[(w++) * kChunk + t];
+        S.e[k] = sS[(w++) * kChunk + t];
+        S.t[k] = sS[(w++) * kChunk + t];
+    }
+    S.nh = sS[(w++) * kChunk + t];
+    S.tr = sS[(w++) * kChunk + t];
+    S.kappa = sS[(w++) * kChunk + t];
+    S.kase = __float_as_int(sS[(w++) * kChunk + t]);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        S.deps[k] = S.s[k] > smin ? 1.0f / S.s[k] : 0.0f;
+        S.ehat[k] = S.eps[k] - S.tr * (1.0f / 3.0f);
+        S.h[k] = 0.0f;
+    }
+}
+
+// a load the compiler may not merge with an earlier one (re-reading is
+// cheaper than keeping the value live across the gather)
+__device__ __forceinline__ float ld_again(const float* p) {
+    float v;
+    asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+// The gather half of the P2G adjoint for one particle: from the grid
+// adjoint (m-bar, mv-bar) at the 27 nodes to gx (added), gv, the adjoint gA of
+// the affine matrix A = stress_scale tau + m_p C, and gmp (added).
+__device__ __forceinline__ void p2g_bwd_gather(const InstDev& I, const AdjArgs& A, const float (&x)[3],
+                                               const float (&v)[3], const float (&Am)[3][3], float (&gx)[3],
+                                               float (&gv)[3], float (&gA)[3][3], float& gmp) {
+    Stencil st;
+    make_stencil(I, x, st);
+    int ox[3], oy[3], oz[3];
+    node_offsets(I, st, ox, oy, oz);
+    const float4* ga = A.gacc + I.node_off;
+    const AxisX lx = axis_x(st, ox);
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        gv[r] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; c++) gA[r][c] = 0.f;
+    }
+#pragma unroll 1
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float wx = lx.w[i], wy = st.w[1][j], wz = st.w[2][k];
+                const float W = wx * wy * wz;
+                const float gW[3] = {lx.dw[i] * wy * wz, wx * st.dw[1][j] * wz, wx * wy * st.dw[2][k]};
+                const float d[3] = {(float(i) - st.fx[0]) * I.dx, (float(j) - st.fx[1]) * I.dx,
+                                    (float(k) - st.fx[2]) * I.dx};
+                const float4 g = ga[lx.o[i] + oy[j] + oz[k]];
+                const float gm = g.x, gmv[3] = {g.y, g.z, g.w};
+                float Wbar = gm * I.mp;
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    const float Ad = Am[r][0] * d[0] + Am[r][1] * d[1] + Am[r][2] * d[2];
+                    Wbar += gmv[r] * (I.mp * v[r] + Ad);
+                    gv[r] += W * I.mp * gmv[r];
+                    gmp += W * gmv[r] * v[r];
+#pragma unroll
+                    for (int c = 0; c < 3; c++) gA[r][c] += W * gmv[r] * d[c];
+                }
+                gmp += W * gm;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const float dbar = W * (Am[0][c] * gmv[0] + Am[1][c] * gmv[1] + Am[2][c] * gmv[2]);
+                    gx[c] += Wbar * gW[c] - dbar;
+                }
+            }
+}
+
+// The chain through the trial F = (I + dt C) F and the stores of the
+// adjoint of state k (in place of the adjoint of state k+1).
+__device__ __forceinline__ void p2g_bwd_finish(const InstDev& I, const AdjArgs& A, long long p, const float (&gx)[3],
+                                               const float (&gv)[3], float (&gC)[3][3], const float (&gFt)[3][3]) {
+    const StepArgs& a = A.f;
+    const long long N = a.ncap;
+    float C[3][3], F[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            C[r][c] = ld_again(a.sin + (kC + 3 * r + c) * N + p);
+            F[r][c] = ld_again(a.sin + (kF + 3 * r + c) * N + p);
+        }
+    float gF[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            gF[r][c] = gFt[r][c] + I.dt * (C[0][r] * gFt[0][c] + C[1][r] * gFt[1][c] + C[2][r] * gFt[2][c]);
+            gC[r][c] += I.dt * (gFt[r][0] * F[c][0] + gFt[r][1] * F[c][1] + gFt[r][2] * F[c][2]);
+        }
+    bool finite = true;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        A.adj[(kX + k) * N + p] = gx[k];
+        A.adj[(kV + k) * N + p] = gv[k];
+        finite = finite && isfinite(gx[k]) && isfinite(gv[k]);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            A.adj[(kC + 3 * r + c) * N + p] = gC[r][c];
+            A.adj[(kF + 3 * r + c) * N + p] = gF[r][c];
+            finite = finite && isfinite(gF[r][c]) && isfinite(gC[r][c]);
+        }
+    if (!finite) atomicOr(a.status, kStatusNonFinite);
+}
+
+// gtau, gC (the affine part), gmp (the A : C part) and the clipped adjoint of F'
+__device__ __forceinline__ void p2g_bwd_affine(const InstDev& I, const AdjArgs& A, long long p, const float (&gA)[3][3],
+                                               float (&gFn)[3][3], float (&gtau)[3][3], float (&gC)[3][3],
+                                               float& gmp) {
+    const StepArgs& a = A.f;
+    const long long N = a.ncap;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float g = ld_again(A.adj + (kF + 3 * r + c) * N + p);
+            gFn[r][c] = a.clip > 0.f ? clipf(g, a.clip) : g;
+            gtau[r][c] = I.stress_scale * gA[r][c];
+            gC[r][c] = I.mp * gA[r][c];
+            gmp += gA[r][c] * ld_again(a.sin + (kC + 3 * r + c) * N + p);
+        }
+}
+
+
+// Adjoint of P2G and of the constitutive step, FP32. A particle whose
+// deformation is ill-conditioned for FP32 (see needs_fp64) is left untouched
+// and listed for k_p2g_bwd_fp64.
+__global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd(AdjArgs A) {
     __shared__ double sred[4 * 32];
+    __shared__ InstDev sI;
+    __shared__ float sS[kParked * kChunk];
     const StepArgs& a = A.f;
     const int inst = a.chunk_inst[blockIdx.x];
-    const InstDev& I = a.inst[inst];
+    const InstDev& I = stage_instance(sI, a.inst, inst);
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
     const bool active = p - I.pbeg < I.n;
     const long long N = a.ncap;
     float gmu = 0.f, glam = 0.f, galpha = 0.f, gmp = 0.f;
     if (active) {
-        float x[3], v[3], C[3][3], F[3][3], gx[3], gFn[3][3];
+        float x[3], v[3], gx[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             x[k] = ld(a.sin, N, kX + k, p);
             v[k] = ld(a.sin, N, kV + k, p);
             gx[k] = A.adj[(kX + k) * N + p];
         }
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                C[r][c] = ld(a.sin, N, kC + 3 * r + c, p);
-                F[r][c] = ld(a.sin, N, kF + 3 * r + c, p);
-                float g = A.adj[(kF + 3 * r + c) * N + p];
-                gFn[r][c] = a.clip > 0.f ? clipf(g, a.clip) : g;
-            }
-        float Ft[3][3];
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-                Ft[r][c] = F[r][c] + I.dt * (C[r][0] * F[0][c] + C[r][1] * F[1][c] + C[r][2] * F[2][c]);
-        Spectral<float> S;
-        constitutive_spectral<float>(Ft, I.mu, I.lam, I.beta, I.smin, S);
-        const bool fb = needs_fp64(S);
-        float Fn[3][3], tau[3][3];
-        if (!fb) spectral_outputs<float, float>(S, Fn, tau);
-        else {
-            constitutive_fp64(Ft, I.mu, I.lam, I.beta, I.smin, Fn, tau);
-        }
+        // forward constitutive step again: the stress for the gather, the
+        // spectral data for the adjoint (parked in shared memory meanwhile)
+        bool fb;
         float Am[3][3];
+        {
+            float C[3][3], Ft[3][3];
+            load_trial(I, a, p, C, Ft);
+            Spectral<float> S;
+            constitutive_spectral<float>(Ft, I.mu, I.lam, I.beta, I.smin, S);
+            fb = needs_fp64(S);
+            float Fn[3][3], tau[3][3];
+            spectral_outputs<float, float>(S, Fn, tau);
+            park(sS, S);
+#pragma unroll
+            for (int r = 0; r < 3; r++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) Am[r][c] = I.stress_scale * tau[r][c] + I.mp * C[r][c];
+        }
+        if (fb) {
+            a.fb_list[atomicAdd(a.fb_count, 1)] = (int)p;
+        } else {
+            float gv[3], gA[3][3];
+            p2g_bwd_gather(I, A, x, v, Am, gx, gv, gA, gmp);
+            float gFn[3][3], gtau[3][3], gC[3][3], gFt[3][3];
+            p2g_bwd_affine(I, A, p, gA, gFn, gtau, gC, gmp);
+            Spectral<float> S;
+            unpark(sS, S, I.smin);
+            constitutive_adjoint_spectral<float>(S, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, gFt, gmu, glam,
+                                                 galpha);
+            p2g_bwd_finish(I, A, p, gx, gv, gC, gFt);
+        }
+    }
+    float gd[4] = {gmu, glam, galpha, gmp};
+    block_reduce_add<4>(gd, A.gmat + 4 * inst, sred);
+}
+
+// The particles k_p2g_bwd listed: the same adjoint with the SVD, the return
+// mapping and their adjoint in FP64.
+__global__ void __launch_bounds__(kFp64Threads) k_p2g_bwd_fp64(AdjArgs A) {
+    __shared__ int scount;
+    const StepArgs& a = A.f;
+    const int count = fb_begin(a.fb_count, &scount);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const long long p = a.fb_list[i];
+        const int inst = a.chunk_inst[p / kChunk];
+        const InstDev& I = a.inst[inst];
+        const long long N = a.ncap;
+        float x[3], v[3], gx[3], C[3][3], Ft[3][3], Fn[3][3], tau[3][3], Am[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            x[k] = ld(a.sin, N, kX + k, p);
+            v[k] = ld(a.sin, N, kV + k, p);
+            gx[k] = A.adj[(kX + k) * N + p];
+        }
+        load_trial(I, a, p, C, Ft);
+        constitutive_fp64(Ft, I.mu, I.lam, I.beta, I.smin, Fn, tau);
 #pragma unroll
         for (int r = 0; r < 3; r++)
 #pragma unroll
             for (int c = 0; c < 3; c++) Am[r][c] = I.stress_scale * tau[r][c] + I.mp * C[r][c];
-        Stencil st;
-        make_stencil(I, x, st);
-        int ox[3], oy[3], oz[3];
-        node_offsets(I, st, ox, oy, oz);
-        const float4* ga = A.gacc + I.node_off;
-        float gv[3] = {0.f, 0.f, 0.f}, gA[3][3] = {{0.f}};
-#pragma unroll 1
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++)
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    const float wx = st.w[0][i], wy = st.w[1][j], wz = st.w[2][k];
-                    const float W = wx * wy * wz;
-                    const float gW[3] = {st.dw[0][i] * wy * wz, wx * st.dw[1][j] * wz, wx * wy * st.dw[2][k]};
-                    const float d[3] = {(float(i) - st.fx[0]) * I.dx, (float(j) - st.fx[1]) * I.dx,
-                                        (float(k) - st.fx[2]) * I.dx};
-                    const float4 g = ga[ox[i] + oy[j] + oz[k]];
-                    const float gm = g.x, gmv[3] = {g.y, g.z, g.w};
-                    float Wbar = gm * I.mp;
-#pragma unroll
-                    for (int r = 0; r < 3; r++) {
-                        const float Ad = Am[r][0] * d[0] + Am[r][1] * d[1] + Am[r][2] * d[2];
-                        Wbar += gmv[r] * (I.mp * v[r] + Ad);
-                        gv[r] += W * I.mp * gmv[r];
-                        gmp += W * gmv[r] * v[r];
-#pragma unroll
-                        for (int c = 0; c < 3; c++) gA[r][c] += W * gmv[r] * d[c];
-                    }
-                    gmp += W * gm;
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        const float dbar = W * (Am[0][c] * gmv[0] + Am[1][c] * gmv[1] + Am[2][c] * gmv[2]);
-                        gx[c] += Wbar * gW[c] - dbar;
-                    }
-                }
-        float gtau[3][3], gC[3][3];
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                gtau[r][c] = I.stress_scale * gA[r][c];
-                gC[r][c] = I.mp * gA[r][c];
-                gmp += gA[r][c] * C[r][c];
-            }
-        float gFt[3][3];
-        if (!fb) {
-            constitutive_adjoint_spectral<float>(S, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, gFt, gmu, glam,
-                                                 galpha);
-        } else {
-            constitutive_adjoint_fp64(Ft, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, tau, gFt, gmu, glam, galpha);
-        }
-        // Ft = (I + dt C) F
-        float gF[3][3];
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                gF[r][c] = gFt[r][c] + I.dt * (C[0][r] * gFt[0][c] + C[1][r] * gFt[1][c] + C[2][r] * gFt[2][c]);
-                gC[r][c] += I.dt * (gFt[r][0] * F[c][0] + gFt[r][1] * F[c][1] + gFt[r][2] * F[c][2]);
-            }
-        bool finite = true;
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            A.adj[(kX + k) * N + p] = gx[k];
-            A.adj[(kV + k) * N + p] = gv[k];
-            finite = finite && isfinite(gx[k]) && isfinite(gv[k]);
-        }
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                A.adj[(kC + 3 * r + c) * N + p] = gC[r][c];
-                A.adj[(kF + 3 * r + c) * N + p] = gF[r][c];
-                finite = finite && isfinite(gF[r][c]) && isfinite(gC[r][c]);
-            }
-        if (!finite) atomicOr(a.status, kStatusNonFinite);
+        float gv[3], gA[3][3], gmp = 0.f, gmu = 0.f, glam = 0.f, galpha = 0.f;
+        p2g_bwd_gather(I, A, x, v, Am, gx, gv, gA, gmp);
+        float gFn[3][3], gtau[3][3], gC[3][3], gFt[3][3];
+        p2g_bwd_affine(I, A, p, gA, gFn, gtau, gC, gmp);
+        constitutive_adjoint_fp64(Ft, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, tau, gFt, gmu, glam, galpha);
+        p2g_bwd_finish(I, A, p, gx, gv, gC, gFt);
+        atomicAdd(A.gmat + 4 * inst + 0, (double)gmu);
+        atomicAdd(A.gmat + 4 * inst + 1, (double)glam);
+        atomicAdd(A.gmat + 4 * inst + 2, (double)galpha);
+        atomicAdd(A.gmat + 4 * inst + 3, (double)gmp);
+        atomicAdd(a.fp64_count, 1ull);
     }
-    float gd[4] = {gmu, glam, galpha, gmp};
-    block_reduce_add<4>(gd, A.gmat + 4 * inst, sred);
+    fb_end(a.fb_count);
 }
 
 __global__ void __launch_bounds__(256) k_grid_clear(AdjArgs A) {
@@ -796,7 +1085,8 @@ static inline int grid_ctas(int n_blocks) { return (n_blocks * 32 + 255) / 256; 
 cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
     const StepArgs& a = A.f;
     const bool particle_kernel = id == KernelId::P2G || id == KernelId::G2P || id == KernelId::G2PBwd ||
-                                 id == KernelId::P2GBwd;
+                                 id == KernelId::P2GBwd || id == KernelId::P2GFp64 ||
+                                 id == KernelId::P2GBwdFp64;
     if ((particle_kernel && a.n_chunks <= 0) || (!particle_kernel && a.n_blocks <= 0)) return cudaSuccess;
     switch (id) {
         case KernelId::P2G: k_p2g<<<a.n_chunks, kChunk, 0, s>>>(a); break;
@@ -806,6 +1096,8 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
         case KernelId::GridBwd: k_grid_bwd<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
         case KernelId::P2GBwd: k_p2g_bwd<<<a.n_chunks, kChunk, 0, s>>>(A); break;
         case KernelId::GridClear: k_grid_clear<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
+        case KernelId::P2GFp64: k_p2g_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(a); break;
+        case KernelId::P2GBwdFp64: k_p2g_bwd_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(A); break;
         case KernelId::SlotClear: {
             AdjArgs C = A;
             C.gacc = nullptr;

@@ -6,7 +6,11 @@
 
 namespace mpm {
 
-enum class KernelId : int { P2G = 0, Grid, G2P, G2PBwd, GridBwd, P2GBwd, GridClear, SlotClear, Count };
+enum class KernelId : int {
+    P2G = 0, Grid, G2P, G2PBwd, GridBwd, P2GBwd, GridClear, SlotClear, P2GFp64, P2GBwdFp64, Count
+};
+constexpr int kFp64Ctas = 152;   // CTAs of the FP64 fix-up kernels (grid-stride over the deferred list)
+constexpr int kFp64Threads = 128;
 
 // one substep kernel; forward kernels read only A.f
 cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s);

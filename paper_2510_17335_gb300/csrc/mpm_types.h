@@ -55,6 +55,8 @@ struct StepArgs {
     unsigned long long* fp64_count;
     float clip;             // > 0: clip adjoints to [-clip, clip]
     int tile;               // 1: sum scatters in a shared-memory tile per CTA
+    int* fb_list;           // particles deferred to the FP64 constitutive kernels [ncap]
+    int* fb_count;          // [0] entries of fb_list, [1] CTA ticket; both zero between launches
 };
 
 // Arguments of one substep's adjoint kernels.

@@ -20,6 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmpm_gb300.so")
 
 MPM_OK = 0
+PROFILE_KERNELS = 10    # MPM_PROFILE_KERNELS of the header
 ERRORS = {
     -1: "MPM_ERR_INVALID_ARG", -2: "MPM_ERR_OOM", -3: "MPM_ERR_CUDA", -4: "MPM_ERR_OUT_OF_DOMAIN",
     -5: "MPM_ERR_NON_FINITE", -6: "MPM_ERR_NO_RECORD", -7: "MPM_ERR_TIMEOUT", -8: "MPM_ERR_NO_DEVICE",
@@ -84,6 +85,7 @@ EXPORTS = {
     "mpm_get_info": (_ip, [_vp, ctypes.POINTER(mpm_info_t)]),
     "mpm_grid_mass": (_ip, [_vp, _dp]),
     "mpm_set_substep": (_ip, [_vp, ctypes.c_int64]),
+    "mpm_autotune": (_ip, [_vp, _ip, ctypes.POINTER(ctypes.c_int)]),
     "mpm_profile": (_ip, [_vp, _ip]),
     "mpm_profile_read": (_ip, [_vp, _ip, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "mpm_kernel_name": (ctypes.c_char_p, [_ip]),
@@ -300,6 +302,11 @@ class Simulation:
     def synchronize(self):
         check(lib().mpm_synchronize(self.h), "mpm_synchronize")
 
+    def autotune(self, trial_substeps: int = 20) -> dict:
+        c = (ctypes.c_int * 2)()
+        check(lib().mpm_autotune(self.h, int(trial_substeps), c), "mpm_autotune")
+        return {"tile_scatter": c[0], "sort_every": c[1]}
+
     def set_substep(self, s: int):
         check(lib().mpm_set_substep(self.h, int(s)), "mpm_set_substep")
 
@@ -309,7 +316,7 @@ class Simulation:
     def profile_read(self) -> dict:
         """{kernel name: (total device ms, launches)} for every kernel."""
         out = {}
-        for k in range(8):
+        for k in range(PROFILE_KERNELS):
             ms = ctypes.c_double()
             n = ctypes.c_int64()
             check(lib().mpm_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)), "mpm_profile_read")

@@ -166,7 +166,8 @@ def batch_uneven(n_inst: int = 64, seed: int = SEED_BASE + 4, n_lo: float = 2e4,
     a x b x a cells with b = round(0.375 a) at 8 per cell, grids log-uniform
     in [r_lo, r_hi] (rounded to a multiple of 4), materials uniform in
     E [5e4, 5e5], nu [0.2, 0.4], phi [25, 40] deg, rho [1200, 2200]; the
-    paper's system-identification trajectory scaled to each bed."""
+    paper's system-identification trajectory scaled to each bed and paced at
+    about 0.5 m/s."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n_inst):
@@ -184,7 +185,8 @@ def batch_uneven(n_inst: int = 64, seed: int = SEED_BASE + 4, n_lo: float = 2e4,
         phi = rng.uniform(25.0, 40.0)
         rho = rng.uniform(1200.0, 2200.0)
         scale = a * dx / 0.28
-        steps = max(1, n_substeps // (4 * 10))
+        # ~0.5 m/s along the first segment (10 substeps of 5e-5 s per step)
+        steps = max(1, int(round(0.09 * scale / (0.5 * 10 * 5e-5))))
         traj = Trajectory(start_pose=(ox + 0.25 * a * dx, top + 0.01, 0.5, 0.0), substeps_per_action=10,
                           actions=sysid_actions(scale, steps))
         out.append(Workload(f"inst{i}_n{x0.shape[0]}_grid{R}", (R, R, R), dx, 5e-5, n_substeps, E, nu, rho, phi,

@@ -72,3 +72,16 @@ def test_invalid_arguments_are_rejected(L):
     assert L.mpm_backward(None, None, None, 0, None, None) == -1
     assert L.mpm_reset(None) == -1
     L.mpm_destroy(None)
+
+
+def test_profile_kernel_table_matches_header(L):
+    hdr = open(os.path.join(ROOT, "include", "mpm.h")).read()
+    n = int(re.search(r"#define MPM_PROFILE_KERNELS (\d+)", hdr).group(1))
+    assert n == mpm.PROFILE_KERNELS
+    names = [L.mpm_kernel_name(k).decode() for k in range(n)]
+    assert all(names) and len(set(names)) == n
+    assert L.mpm_kernel_name(n) == b"" and L.mpm_kernel_name(-1) == b""
+    # every id the header lists in its profile comment names the same kernel
+    for k, name in re.findall(r"(\d+) (k_[a-z0-9_]+)", hdr):
+        if int(k) < n:
+            assert names[int(k)] == name, (k, name)

@@ -288,3 +288,21 @@ def test_sorted_scrambled_order_matches_oracle():
             g = sim.get_state()
         ref = oracle_rollout(w, 10)
         _compare(g, ref, 10, f"bed8k scrambled, sort_every={sort_every}")
+
+
+def test_autotune_restores_state_and_keeps_parity():
+    """mpm_autotune times its candidates from the current state and restores
+    it; the tuned handle still matches the oracle."""
+    w = W.cfg_small()
+    with mpm.simulation_from_workloads([w]) as sim:
+        sim.forward(3)
+        before = sim.get_state()
+        choice = sim.autotune(6)
+        after = sim.get_state()
+        for k in before:
+            assert np.array_equal(before[k], after[k]), k
+        assert choice["tile_scatter"] in (0, 1) and choice["sort_every"] >= 0
+        sim.forward(7)
+        g = sim.get_state()
+    ref = oracle_rollout(w, 10)
+    _compare(g, ref, 10, f"bed8k after autotune {choice}")
