@@ -45,7 +45,32 @@ template <typename T> MPM_HD __forceinline__ T jacobi_tiny();
 template <> MPM_HD __forceinline__ float jacobi_tiny<float>() { return 1e-35f; }
 template <> MPM_HD __forceinline__ double jacobi_tiny<double>() { return 1e-300; }
 template <typename T> struct Sweeps;
-template <> struct Sweeps<float> { static constexpr int n = 4; };
+#ifndef MPM_SVD_SWEEPS
+#define MPM_SVD_SWEEPS 4
+#endif
+template <> struct Sweeps<float> { static constexpr int n = MPM_SVD_SWEEPS; };
+
+// 1/sqrt(x) and 1/x for FP32 without the branches of the IEEE operations:
+// the hardware approximation (device) refined by one Newton step, which
+// brings it to about an ulp. The host, which compiles this code for the CPU
+// test of the kernels' arithmetic, uses the exact operations.
+MPM_HD __forceinline__ float rsqrt_nr(float x) {
+#if defined(__CUDA_ARCH__)
+    const float y = rsqrtf(x);
+    return y * fmaf(-0.5f * x, y * y, 1.5f);
+#else
+    return 1.0f / sqrtf(x);
+#endif
+}
+// for |x| in [2^-126, 2^126]
+MPM_HD __forceinline__ float rcp_nr(float x) {
+#if defined(__CUDA_ARCH__)
+    const float y = __fdividef(1.0f, x);
+    return fmaf(y, fmaf(-x, y, 1.0f), y);
+#else
+    return 1.0f / x;
+#endif
+}
 template <> struct Sweeps<double> { static constexpr int n = 10; };
 
 // ---------------------------------------------------------------------------
@@ -78,8 +103,42 @@ MPM_HD __forceinline__ T dot3_minus(T x0, T y0, T x1, T y1, T x2, T y2, T shift)
     return s + (((c1 + c2) + c3) + ((e0 + e1) + e2));
 }
 
+// FP32 rotation: tan(theta) = sgn(d) e / (|d| + sqrt(d^2 + e^2)) with
+// d = g_qq - g_pp, e = 2 g_pq, both first scaled by 1/max(|d|, |e|) (the
+// quotient does not depend on that scale, so the reciprocal need not be
+// exact) so that nothing under- or overflows; then no division, square root
+// or branch remains. The diagonal update is Rutishauser's g -/+ t g_pq.
+template <int p, int q, int r>
+MPM_HD __forceinline__ void jacobi_rotate_f32(float (&G)[3][3], float (&V)[3][3]) {
+    const float gpq = G[p][q], gpp = G[p][p], gqq = G[q][q];
+    const bool on = fabsf(gpq) > jacobi_tiny<float>();
+    const float d = gqq - gpp, e = 2.0f * gpq;
+    const float inv = rcp_nr(on ? fmaxf(fabsf(d), fabsf(e)) : 1.0f);
+    const float dn = d * inv, en = e * inv;
+    const float r2 = fmaf(dn, dn, en * en);   // in [1, 2]
+    const float root = r2 * rsqrt_nr(r2);
+    float t = (d >= 0.0f ? en : -en) * rcp_nr(fabsf(dn) + root);
+    t = on ? t : 0.0f;
+    const float c = rsqrt_nr(fmaf(t, t, 1.0f)), s = c * t;
+    G[p][p] = fmaf(-t, gpq, gpp);
+    G[q][q] = fmaf(t, gpq, gqq);
+    G[p][q] = G[q][p] = on ? 0.0f : gpq;
+    const float grp = G[r][p], grq = G[r][q];
+    G[r][p] = G[p][r] = c * grp - s * grq;
+    G[r][q] = G[q][r] = s * grp + c * grq;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float a = V[k][p], b = V[k][q];
+        V[k][p] = c * a - s * b;
+        V[k][q] = s * a + c * b;
+    }
+}
+
 template <typename T, int p, int q, int r>
 MPM_HD __forceinline__ void jacobi_rotate(T (&G)[3][3], T (&V)[3][3]) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+        jacobi_rotate_f32<p, q, r>(G, V);
+    } else {
     const T gpq = G[p][q], gpp = G[p][p], gqq = G[q][q];
     if (!(fabs(gpq) > jacobi_tiny<T>())) return;
     const T zeta = (gqq - gpp) / (T(2) * gpq);
@@ -101,7 +160,14 @@ MPM_HD __forceinline__ void jacobi_rotate(T (&G)[3][3], T (&V)[3][3]) {
         V[k][p] = c * a - s * b;
         V[k][q] = s * a + c * b;
     }
+    }
 }
+
+// 1/sqrt(x) and 1/x: FP32 through rsqrt_nr / rcp_nr, FP64 exact
+template <typename T> MPM_HD __forceinline__ T rsqrt_t(T x) { return T(1) / dsqrt<T>(x); }
+template <> MPM_HD __forceinline__ float rsqrt_t<float>(float x) { return rsqrt_nr(x); }
+template <typename T> MPM_HD __forceinline__ T rcp_t(T x) { return T(1) / x; }
+template <> MPM_HD __forceinline__ float rcp_t<float>(float x) { return rcp_nr(x); }
 
 // h[k] = sigma_k^2 - 1 to full relative accuracy
 template <typename T>
@@ -147,7 +213,9 @@ MPM_HD __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3], T 
         bm[r] = (m == 0) ? b[r][0] : ((m == 1) ? b[r][1] : b[r][2]);
     }
     T ui[3], uj[3], um[3];
-    T si = dsqrt<T>(bi[0] * bi[0] + bi[1] * bi[1] + bi[2] * bi[2]);
+    const T ni = bi[0] * bi[0] + bi[1] * bi[1] + bi[2] * bi[2];
+    const T inv_si = rsqrt_t<T>(ni);
+    const T si = ni * inv_si;
     if (!(si > T(1e-30))) {
         // F == 0: any rotations will do
 #pragma unroll
@@ -158,13 +226,14 @@ MPM_HD __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3], T 
         h[0] = h[1] = h[2] = T(-1);
         return;
     }
-    const T inv_si = T(1) / si;
 #pragma unroll
     for (int r = 0; r < 3; r++) ui[r] = bi[r] * inv_si;
     const T dij = ui[0] * bj[0] + ui[1] * bj[1] + ui[2] * bj[2];
 #pragma unroll
     for (int r = 0; r < 3; r++) uj[r] = bj[r] - dij * ui[r];
-    T sj = dsqrt<T>(uj[0] * uj[0] + uj[1] * uj[1] + uj[2] * uj[2]);
+    const T nj = uj[0] * uj[0] + uj[1] * uj[1] + uj[2] * uj[2];
+    const T inv_sj = rsqrt_t<T>(nj);
+    T sj = nj * inv_sj;
     if (!(sj > T(1e-30) * si)) {
         // rank one: any unit vector orthogonal to u_i
         // (static indices only: a runtime index would put the caller's arrays in local memory)
@@ -179,9 +248,8 @@ MPM_HD __forceinline__ void svd3(const T (&F)[3][3], T (&U)[3][3], T (&s)[3], T 
         for (int r = 0; r < 3; r++) uj[r] /= ne;
         sj = uj[0] * bj[0] + uj[1] * bj[1] + uj[2] * bj[2];
     } else {
-        const T inv = T(1) / sj;
 #pragma unroll
-        for (int r = 0; r < 3; r++) uj[r] *= inv;
+        for (int r = 0; r < 3; r++) uj[r] *= inv_sj;
         sj = uj[0] * bj[0] + uj[1] * bj[1] + uj[2] * bj[2];
     }
     // u_m completes a right-handed frame: (i, j, m) cyclic -> u_i x u_j
@@ -228,7 +296,7 @@ MPM_HD __forceinline__ void return_map(Spectral<T>& S, T mu, T lam, T beta, T sm
         const bool ok = S.s[k] > smin;
         // ln s = 0.5 log1p(s^2 - 1), exact for s near 1
         S.eps[k] = ok ? T(0.5) * dlog1p<T>(S.h[k]) : dlog<T>(smin);
-        S.deps[k] = ok ? T(1) / S.s[k] : T(0);
+        S.deps[k] = ok ? rcp_t<T>(S.s[k]) : T(0);
         S.tr += S.eps[k];
     }
     T n2 = T(0);
@@ -250,13 +318,14 @@ MPM_HD __forceinline__ void return_map(Spectral<T>& S, T mu, T lam, T beta, T sm
         for (int k = 0; k < 3; k++) { S.shat[k] = S.s[k]; S.e[k] = S.eps[k]; }
     } else {
         S.kase = 2;
-        const T r = dg / S.nh;
+        const T inv_nh = rcp_t<T>(S.nh);
+        const T r = dg * inv_nh;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             S.e[k] = S.eps[k] - r * S.ehat[k];
             S.shat[k] = dexp<T>(S.e[k]);
         }
-        S.kappa = -beta * S.tr / S.nh;
+        S.kappa = -beta * S.tr * inv_nh;
     }
     const T se = S.e[0] + S.e[1] + S.e[2];
 #pragma unroll
@@ -328,10 +397,14 @@ MPM_HD __forceinline__ bool constitutive(const float (&Ft)[3][3], float mu, floa
 // the isotropic maps s -> shat and s -> t. The first quotient is evaluated
 // through expm1 so that it stays exact at s_i = s_j.
 // ---------------------------------------------------------------------------
+// x / expm1(x) and expm1(k x) / expm1(x), given em = expm1(x); below
+// |x| = 1e-30 they equal their limits 1 and k to working precision
 template <typename T>
-MPM_HD __forceinline__ T xm1(T x) { return x == T(0) ? T(1) : x / dexpm1<T>(x); }
+MPM_HD __forceinline__ T xm1(T x, T em) { return fabs(x) < T(1e-30) ? T(1) : x * rcp_t<T>(em); }
 template <typename T>
-MPM_HD __forceinline__ T em1ratio(T k, T x) { return x == T(0) ? k : dexpm1<T>(k * x) / dexpm1<T>(x); }
+MPM_HD __forceinline__ T em1ratio(T k, T x, T em) {
+    return fabs(x) < T(1e-30) ? k : dexpm1<T>(k * x) * rcp_t<T>(em);
+}
 
 template <typename T>
 MPM_HD __forceinline__ void constitutive_adjoint_spectral(const Spectral<T>& S, T mu, T lam, T alpha, T beta,
@@ -368,7 +441,7 @@ MPM_HD __forceinline__ void constitutive_adjoint_spectral(const Spectral<T>& S, 
 #pragma unroll
         for (int i = 0; i < 3; i++) sb[i] = G[i][i] + (T(2) * mu * tb[i] + lam * stb) * S.deps[i];
     } else if (S.kase == 2) {
-        const T inv_nh = T(1) / S.nh;
+        const T inv_nh = rcp_t<T>(S.nh);
         T eb[3], eh[3];
 #pragma unroll
         for (int i = 0; i < 3; i++) {
@@ -405,29 +478,38 @@ MPM_HD __forceinline__ void constitutive_adjoint_spectral(const Spectral<T>& S, 
         const T dsig = si - sj;
         T sum = si + sj;
         if (fabs(sum) < T(1e-30)) sum = T(1e-30);
+        const T inv_sum = rcp_t<T>(sum);
+        // 1/s_j where smooth (s_j > smin)
+        const T inv_sj = S.deps[j];
         // clamped singular values (below smin) only: plain quotients, 0 when equal
         const bool sep = fabs(dsig) > T(1e-30);
         T ds, dd, q1;
         if (S.kase == 0) {
             ds = T(0);
-            dd = T(2) / sum;
+            dd = T(2) * inv_sum;
             q1 = T(0);
         } else if (S.kase == 1) {
             ds = T(1);
             dd = T(1);
-            q1 = smooth ? T(2) * mu * xm1<T>(S.eps[i] - S.eps[j]) / sj : (sep ? (S.t[i] - S.t[j]) / dsig : T(0));
+            if (smooth) {
+                const T D = S.eps[i] - S.eps[j];
+                q1 = T(2) * mu * xm1<T>(D, dexpm1<T>(D)) * inv_sj;
+            } else {
+                q1 = sep ? (S.t[i] - S.t[j]) / dsig : T(0);
+            }
         } else {
             if (smooth) {
                 const T D = S.eps[i] - S.eps[j];
-                ds = S.shat[j] / sj * em1ratio<T>(S.kappa, D);
-                q1 = T(2) * mu * S.kappa * xm1<T>(D) / sj;
+                const T em = dexpm1<T>(D);
+                ds = S.shat[j] * inv_sj * em1ratio<T>(S.kappa, D, em);
+                q1 = T(2) * mu * S.kappa * xm1<T>(D, em) * inv_sj;
             } else {
                 ds = sep ? (S.shat[i] - S.shat[j]) / dsig : T(0);
                 q1 = sep ? (S.t[i] - S.t[j]) / dsig : T(0);
             }
-            dd = (S.shat[i] + S.shat[j]) / sum;
+            dd = (S.shat[i] + S.shat[j]) * inv_sum;
         }
-        const T q2 = (S.t[i] - S.t[j]) / sum;
+        const T q2 = (S.t[i] - S.t[j]) * inv_sum;
         const T a = T(0.5) * (ds + dd), b = T(0.5) * (ds - dd);
         const T Gij = G[i][j], Gji = G[j][i];
         const T St = Th[i][j] + Th[j][i];
@@ -671,6 +753,21 @@ __device__ __forceinline__ void block_reduce_add(float (&v)[NV], double* dst, do
         for (int w = 0; w < nw; w++) x += sred[threadIdx.x * 32 + w];
         if (x != 0.0) atomicAdd(dst + threadIdx.x, x);
     }
+}
+
+// Sum v over the warp and add it to dst (FP64 atomics, lane 0) when any lane
+// has any: all 32 lanes must call it.
+template <int NV>
+__device__ __forceinline__ void warp_reduce_add(float (&v)[NV], double* dst, bool any) {
+    if (!__any_sync(0xffffffffu, any)) return;
+#pragma unroll
+    for (int k = 0; k < NV; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < NV; k++)
+            if (v[k] != 0.0f) atomicAdd(dst + k, (double)v[k]);
 }
 
 // ---------------------------------------------------------------------------

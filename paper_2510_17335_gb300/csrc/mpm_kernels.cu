@@ -20,7 +20,8 @@
 #include "mpm_device.cuh"
 #include "mpm_launch.h"
 
-// minimum resident CTAs per SM of the particle kernels (register caps)
+// minimum resident CTAs per SM of the particle kernels (register caps; the
+// defaults are the fastest of a measured sweep on the 1M-particle bed)
 #ifndef MPM_MINB_P2G
 #define MPM_MINB_P2G 3
 #endif
@@ -30,11 +31,8 @@
 #ifndef MPM_MINB_G2P_BWD
 #define MPM_MINB_G2P_BWD 3
 #endif
-#ifndef MPM_MARK_COND
-#define MPM_MARK_COND 1
-#endif
 #ifndef MPM_MINB_P2G_BWD
-#define MPM_MINB_P2G_BWD 2
+#define MPM_MINB_P2G_BWD 3
 #endif
 
 namespace mpm {
@@ -90,14 +88,9 @@ __device__ __forceinline__ void mark_blocks(const InstDev& I, const Stencil& st,
     for (int bx = b0x; bx <= b1x; bx++)
         for (int by = b0y; by <= b1y; by++)
             for (int bz = b0z; bz <= b1z; bz++) {
-#if MPM_MARK_COND
-            {
+                // test first: the load mostly hits L1, a store always goes to L2
                 unsigned char* f = flags + I.blk_off + (bx * I.nb[1] + by) * I.nb[2] + bz;
                 if (*f == 0) *f = 1;
-            }
-#else
-                flags[I.blk_off + (bx * I.nb[1] + by) * I.nb[2] + bz] = 1;
-#endif
             }
 }
 
@@ -386,7 +379,6 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
 // adjoint
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A) {
-    __shared__ double sred[8 * 32];
     __shared__ TileSmem T;
     __shared__ InstDev sI;
     const StepArgs& a = A.f;
@@ -395,7 +387,6 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A)
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
     const bool active = p - I.pbeg < I.n;
     const long long N = a.ncap;
-    float gp[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float x[3] = {0.5f, 0.5f, 0.5f};
     if (active) {
 #pragma unroll
@@ -406,46 +397,57 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A)
     if (a.tile) tile_begin(T, active, st, kChunk);
     else if (threadIdx.x == 0) T.tiled = 0;
     if (!a.tile) __syncthreads();
+    int ox[3], oy[3], oz[3];
+    node_offsets(I, st, ox, oy, oz);
+    const float4* vg = a.vout + I.node_off;
+    float gx[3] = {0.f, 0.f, 0.f}, gvn[3] = {0.f, 0.f, 0.f};
     if (active) {
-        float gx[3], gv[3], gC[3][3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             gx[k] = A.adj[(kX + k) * N + p];
-            gv[k] = A.adj[(kV + k) * N + p];
-            if (a.clip > 0.f) { gx[k] = clipf(gx[k], a.clip); gv[k] = clipf(gv[k], a.clip); }
+            float gv = A.adj[(kV + k) * N + p];
+            if (a.clip > 0.f) { gx[k] = clipf(gx[k], a.clip); gv = clipf(gv, a.clip); }
+            // adjoint of the advection x' = x + dt v'
+            gvn[k] = gv + I.dt * gx[k];
         }
+    }
+    if (I.pcoll && I.shovel_on) {   // uniform over the CTA
+        // Particle-level shovel contact. Outside the shovel it is the
+        // identity; inside, its adjoint needs the pre-contact G2P velocity,
+        // gathered again here for those particles only.
+        float gp[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool contact = false;
+        if (active) {
+            const Pose P = load_pose(I, a.substep);
+            float sn, cs, n[3], nl[3];
+            sincosf(P.psi, &sn, &cs);
+            if (shovel_inside(I, P, cs, sn, x, n, nl)) {
+                contact = true;
+                float v[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < 3; i++)
+#pragma unroll
+                    for (int j = 0; j < 3; j++)
+#pragma unroll
+                        for (int k = 0; k < 3; k++) {
+                            const float W = st.w[0][i] * st.w[1][j] * st.w[2][k];
+                            const float4 g = __ldg(vg + ox[i] + oy[j] + oz[k]);
+                            v[0] += W * g.x; v[1] += W * g.y; v[2] += W * g.z;
+                        }
+                float g0[3] = {gvn[0], gvn[1], gvn[2]}, gq[3] = {0.f, 0.f, 0.f};
+                gvn[0] = gvn[1] = gvn[2] = 0.f;
+                shovel_project_adj(I, P, cs, sn, x, v, g0, gvn, gq, gp);
+                gx[0] += gq[0]; gx[1] += gq[1]; gx[2] += gq[2];
+            }
+        }
+        warp_reduce_add<8>(gp, A.gpose + 8 * inst, contact);
+    }
+    if (active) {
+        float gC[3][3];
 #pragma unroll
         for (int r = 0; r < 3; r++)
 #pragma unroll
             for (int c = 0; c < 3; c++) gC[r][c] = A.adj[(kC + 3 * r + c) * N + p];
-        int ox[3], oy[3], oz[3];
-        node_offsets(I, st, ox, oy, oz);
-        const float4* vg = a.vout + I.node_off;
-        // adjoint of the advection x' = x + dt v'
-        float gvn[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++) gvn[k] = gv[k] + I.dt * gx[k];
-        if (I.pcoll && I.shovel_on) {
-            // the contact needs the pre-contact G2P velocity
-            float v[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++)
-#pragma unroll
-                    for (int k = 0; k < 3; k++) {
-                        const float W = sel3(st.w[0], i) * st.w[1][j] * st.w[2][k];
-                        const float4 g = __ldg(vg + sel3(ox, i) + oy[j] + oz[k]);
-                        v[0] += W * g.x; v[1] += W * g.y; v[2] += W * g.z;
-                    }
-            const Pose P = load_pose(I, a.substep);
-            float sn, cs;
-            sincosf(P.psi, &sn, &cs);
-            float g0[3] = {gvn[0], gvn[1], gvn[2]}, gq[3] = {0.f, 0.f, 0.f};
-            gvn[0] = gvn[1] = gvn[2] = 0.f;
-            shovel_project_adj(I, P, cs, sn, x, v, g0, gvn, gq, gp);
-            gx[0] += gq[0]; gx[1] += gq[1]; gx[2] += gq[2];
-        }
         // adjoint of the APIC gather: scatter into the grid velocity adjoint
         const float kap = 4.0f * I.inv_dx * I.inv_dx;
         float4* ga = A.gacc + I.node_off;
@@ -484,7 +486,6 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A)
         for (int k = 0; k < 3; k++) A.adj[(kX + k) * N + p] = gx[k];
     }
     tile_flush(T, I, A.gacc, nullptr, kChunk);
-    if (I.pcoll && I.shovel_on) block_reduce_add<8>(gp, A.gpose + 8 * inst, sred);
 }
 
 __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
