@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--substeps", type=int, default=100)
-    ap.add_argument("--checkpoint", type=int, default=50)
+    ap.add_argument("--checkpoint", type=int, default=0,
+                    help="checkpoint interval K (0: the largest K <= substeps whose record fits half the free HBM)")
     ap.add_argument("--start", type=int, default=600, help="substep of the rollout start state")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -234,6 +235,15 @@ def batched_vs_serial(n_inst: int, nsub: int, steps: int, sort_every: int):
 # --------------------------------------------------------------------------
 # our implementation
 # --------------------------------------------------------------------------
+def auto_checkpoint(S: int, slot_state: int, slot_grid: int, free_bytes: int) -> int:
+    """The largest checkpoint interval K <= S whose recorded segment (K + 1
+    states and K grids) takes at most half the free device memory: with
+    K = S the backward reverses the recorded rollout without recomputing it."""
+    budget = free_bytes // 2
+    K = (budget - slot_state) // (slot_state + slot_grid)
+    return int(max(1, min(S, K)))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -253,7 +263,11 @@ def run_ours(args):
             dist.barrier()
 
     w = W.cfg_1m()
-    N, S, K = w.n, args.substeps, args.checkpoint
+    N, S = w.n, args.substeps
+    nodes = int(np.prod([-(-r // 4) * 4 for r in w.res]))
+    slot_state, slot_grid = 96 * N, 32 * nodes + nodes // 64
+    K = args.checkpoint or auto_checkpoint(S, slot_state, slot_grid, torch.cuda.mem_get_info(local)[0])
+    record_bytes = (K + 1) * slot_state + K * slot_grid
     stream = torch.cuda.Stream()
     opts = mpm.make_options(checkpoint_every=K, tile_scatter=args.tile, sort_every=args.sort)
     sim = mpm.simulation_from_workloads([w], opts)
@@ -381,21 +395,25 @@ def run_ours(args):
     avg_s = tot_ms / 1e3 / max(nl, 1)
     kernels = {k: {"ms_total": round(v[0], 3), "launches": v[1],
                    "share": round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)} for k, v in prof.items()}
-    roof = None
+    roof = alu = None
     if name in ALGO_BYTES:
         algo = ALGO_BYTES[name] * N
         ach = algo / avg_s / 1e9
-        traffic = None
-        tf = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-        if os.path.exists(tf):
-            for line in open(tf):
-                f = line.split()
-                if len(f) >= 3 and not line.startswith("#") and f[0] == name and f[1] == kernel_source_sha():
-                    traffic = int(f[2])
+        cnt = kernel_counters(name)
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-                "traffic": traffic, "kernel": name, "algo_bytes_per_launch": algo,
+                "traffic": cnt["dram_bytes"] if cnt else None, "kernel": name, "algo_bytes_per_launch": algo,
                 "avg_launch_us": round(avg_s * 1e6, 2), "peak_kind": f"{peak_kind} hbm_gbs",
                 "timing": "CUDA events around every launch, repetition of the timed steps"}
+        if cnt:
+            # the second limit: FP32 arithmetic and instruction issue, from the
+            # executed counts of one ncu capture and the live duration
+            fl = cnt["fp32_flops"] / avg_s / 1e12
+            ins = cnt["warp_insts"] / avg_s
+            alu = {"kernel": name, "fp32_tflops": round(fl, 2), "fp32_peak_tflops": round(FP32_PEAK_TFLOPS, 1),
+                   "fp32_frac": round(fl / FP32_PEAK_TFLOPS, 4), "warp_insts_per_s": round(ins, -6),
+                   "issue_peak_per_s": ISSUE_PEAK, "issue_frac": round(ins / ISSUE_PEAK, 4),
+                   "counts": "executed per launch (ncu, profiles/kernel_counters.txt)",
+                   "peaks": "152 SMs x 128 FP32 lanes x 2 flop, 152 x 4 schedulers x 1 warp-instruction, at 2.07 GHz"}
     batch = None
     if args.batch > 0:
         batch = batched_vs_serial(args.batch, args.batch_substeps, 2, args.sort)
@@ -411,16 +429,37 @@ def run_ours(args):
         "config": {"workload": "bed1m_grid128: 1,048,576 particles, 128^3 grid, skill-driven box shovel",
                    "substeps_per_step": S, "checkpoint_every": K, "start_substep": args.start,
                    "tile_scatter": args.tile, "sort_every": args.sort,
-                   "l2": "inputs larger than L2 (96 MB state + 4.9 GB segment buffers per step)",
+                   "record_bytes": record_bytes,
+                   "l2": f"inputs larger than L2 (96 MB state, {record_bytes / 1e9:.1f} GB of recorded states and grids per step)",
                    "parallelism": f"replicas x{ws}"},
         "fwd_value": fwd_value, "fwd_ms_per_step": fms / args.steps,
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "roofline": roof, "alu": alu, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "batched_vs_serial": batch,
         "kernels": kernels, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+SM_CLOCK_HZ = 2.07e9
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * SM_CLOCK_HZ / 1e12     # 80.5
+ISSUE_PEAK = 152 * 4 * SM_CLOCK_HZ                        # warp-instructions/s
+
+
+def kernel_counters(name: str):
+    """Per-launch DRAM bytes, executed FP32 flops and warp instructions of a
+    kernel from profiles/kernel_counters.txt, while its sources still hash to
+    the recorded sha (else None: the counters are stale)."""
+    tf = os.path.join(ROOT, "profiles", "kernel_counters.txt")
+    if not os.path.exists(tf):
+        return None
+    sha = kernel_source_sha()
+    for line in open(tf):
+        f = line.split()
+        if len(f) >= 5 and not line.startswith("#") and f[0] == name and f[1] == sha:
+            return {"dram_bytes": int(f[2]), "fp32_flops": int(f[3]), "warp_insts": int(f[4])}
+    return None
 
 
 def kernel_source_sha() -> str:

@@ -122,26 +122,29 @@ __device__ __forceinline__ void p2g_scatter(TileSmem* T, const InstDev& I, float
                                             const float (&v)[3], const float (&A)[3][3]) {
     int ox[3], oy[3], oz[3];
     node_offsets(I, st, ox, oy, oz);
-    float mv[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) mv[k] = I.mp * v[k];
     float4* acc = grid + I.node_off;
 #pragma unroll 1
     for (int i = 0; i < 3; i++) {
         const float dxi = (float(i) - st.fx[0]) * I.dx;
+        float ai[3];   // m_p v + A d, hoisted over the loops
+#pragma unroll
+        for (int r = 0; r < 3; r++) ai[r] = fmaf(A[r][0], dxi, I.mp * v[r]);
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             const float dyj = (float(j) - st.fx[1]) * I.dx;
             const float wij = sel3(st.w[0], i) * st.w[1][j];
+            float aij[3];
+#pragma unroll
+            for (int r = 0; r < 3; r++) aij[r] = fmaf(A[r][1], dyj, ai[r]);
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 const float dzk = (float(k) - st.fx[2]) * I.dx;
                 const float W = wij * st.w[2][k];
                 float4 val;
                 val.x = W * I.mp;
-                val.y = W * (mv[0] + A[0][0] * dxi + A[0][1] * dyj + A[0][2] * dzk);
-                val.z = W * (mv[1] + A[1][0] * dxi + A[1][1] * dyj + A[1][2] * dzk);
-                val.w = W * (mv[2] + A[2][0] * dxi + A[2][1] * dyj + A[2][2] * dzk);
+                val.y = W * fmaf(A[0][2], dzk, aij[0]);
+                val.z = W * fmaf(A[1][2], dzk, aij[1]);
+                val.w = W * fmaf(A[2][2], dzk, aij[2]);
                 if (T) tile_add(*T, acc, sel3(ox, i) + oy[j] + oz[k], st, i, j, k, val, 4);
                 else atomicAdd(acc + sel3(ox, i) + oy[j] + oz[k], val);
             }
@@ -319,25 +322,38 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
     int ox[3], oy[3], oz[3];
     node_offsets(I, st, ox, oy, oz);
     const float4* vg = a.vout + I.node_off;
+    // v = sum W v_node and B = sum W v_node (o - f)^T, summed over k first:
+    // T0 = sum_k wz v_node, T1 = sum_k wz (k - fz) v_node per (i, j)
     float v[3] = {0.0f, 0.0f, 0.0f}, B[3][3] = {{0.0f}};
+    float wzd[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) wzd[k] = st.w[2][k] * (float(k) - st.fx[2]);
 #pragma unroll 1
     for (int i = 0; i < 3; i++) {
         const float di = float(i) - st.fx[0];
+        const float wx = sel3(st.w[0], i);
+        const int oxi = sel3(ox, i);
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             const float dj = float(j) - st.fx[1];
-            const float wij = sel3(st.w[0], i) * st.w[1][j];
+            float T0[3] = {0.f, 0.f, 0.f}, T1[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                const float dk = float(k) - st.fx[2];
-                const float W = wij * st.w[2][k];
-                const float4 g = __ldg(vg + sel3(ox, i) + oy[j] + oz[k]);
-                v[0] += W * g.x;
-                v[1] += W * g.y;
-                v[2] += W * g.z;
-                B[0][0] += W * g.x * di; B[0][1] += W * g.x * dj; B[0][2] += W * g.x * dk;
-                B[1][0] += W * g.y * di; B[1][1] += W * g.y * dj; B[1][2] += W * g.y * dk;
-                B[2][0] += W * g.z * di; B[2][1] += W * g.z * dj; B[2][2] += W * g.z * dk;
+                const float4 g = __ldg(vg + oxi + oy[j] + oz[k]);
+                const float gg[3] = {g.x, g.y, g.z};
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    T0[r] = fmaf(st.w[2][k], gg[r], T0[r]);
+                    T1[r] = fmaf(wzd[k], gg[r], T1[r]);
+                }
+            }
+            const float wxy = wx * st.w[1][j], wxyi = wxy * di, wxyj = wxy * dj;
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+                v[r] = fmaf(wxy, T0[r], v[r]);
+                B[r][0] = fmaf(wxyi, T0[r], B[r][0]);
+                B[r][1] = fmaf(wxyj, T0[r], B[r][1]);
+                B[r][2] = fmaf(wxy, T1[r], B[r][2]);
             }
         }
     }
@@ -448,40 +464,53 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A)
         for (int r = 0; r < 3; r++)
 #pragma unroll
             for (int c = 0; c < 3; c++) gC[r][c] = A.adj[(kC + 3 * r + c) * N + p];
-        // adjoint of the APIC gather: scatter into the grid velocity adjoint
+        // adjoint of the APIC gather: scatter W b into the grid velocity
+        // adjoint with b = gvn + kap gC d (hoisted over the loops); the terms
+        // of gx through d sum to -kap gC^T Sv with Sv = sum W v_node
         const float kap = 4.0f * I.inv_dx * I.inv_dx;
+        float kgC[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) kgC[r][c] = kap * gC[r][c];
+        float Sv[3] = {0.f, 0.f, 0.f};
         float4* ga = A.gacc + I.node_off;
         const AxisX lx = axis_x(st, ox);
 #pragma unroll 1
-        for (int i = 0; i < 3; i++)
+        for (int i = 0; i < 3; i++) {
+            const float wx = lx.w[i], dwx = lx.dw[i], dxi = (float(i) - st.fx[0]) * I.dx;
+            float bi[3];
 #pragma unroll
-            for (int j = 0; j < 3; j++)
+            for (int r = 0; r < 3; r++) bi[r] = fmaf(kgC[r][0], dxi, gvn[r]);
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const float wy = st.w[1][j], dyj = (float(j) - st.fx[1]) * I.dx;
+                const float wxy = wx * wy, gwx = dwx * wy, gwy = wx * st.dw[1][j];
+                float bij[3];
+#pragma unroll
+                for (int r = 0; r < 3; r++) bij[r] = fmaf(kgC[r][1], dyj, bi[r]);
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
-                    const float wx = lx.w[i], wy = st.w[1][j], wz = st.w[2][k];
-                    const float W = wx * wy * wz;
-                    const float gW[3] = {lx.dw[i] * wy * wz, wx * st.dw[1][j] * wz, wx * wy * st.dw[2][k]};
-                    const float d[3] = {(float(i) - st.fx[0]) * I.dx, (float(j) - st.fx[1]) * I.dx,
-                                        (float(k) - st.fx[2]) * I.dx};
+                    const float wz = st.w[2][k], dzk = (float(k) - st.fx[2]) * I.dx;
+                    const float W = wxy * wz;
                     const float4 g = __ldg(vg + lx.o[i] + oy[j] + oz[k]);
-                    const float vi[3] = {g.x, g.y, g.z};
-                    float Cd[3];
+                    float b[3];
 #pragma unroll
-                    for (int r = 0; r < 3; r++) Cd[r] = gC[r][0] * d[0] + gC[r][1] * d[1] + gC[r][2] * d[2];
-                    float4 contrib;
-                    contrib.x = W * (gvn[0] + kap * Cd[0]);
-                    contrib.y = W * (gvn[1] + kap * Cd[1]);
-                    contrib.z = W * (gvn[2] + kap * Cd[2]);
-                    contrib.w = 0.f;
-                    tile_add(T, ga, lx.o[i] + oy[j] + oz[k], st, i, j, k, contrib, 3);
-                    const float Wbar = vi[0] * (gvn[0] + kap * Cd[0]) + vi[1] * (gvn[1] + kap * Cd[1]) +
-                                       vi[2] * (gvn[2] + kap * Cd[2]);
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        const float dbar = kap * W * (gC[0][c] * vi[0] + gC[1][c] * vi[1] + gC[2][c] * vi[2]);
-                        gx[c] += Wbar * gW[c] - dbar;
-                    }
+                    for (int r = 0; r < 3; r++) b[r] = fmaf(kgC[r][2], dzk, bij[r]);
+                    tile_add(T, ga, lx.o[i] + oy[j] + oz[k], st, i, j, k,
+                             make_float4(W * b[0], W * b[1], W * b[2], 0.f), 3);
+                    const float Wbar = g.x * b[0] + g.y * b[1] + g.z * b[2];
+                    gx[0] = fmaf(Wbar, gwx * wz, gx[0]);
+                    gx[1] = fmaf(Wbar, gwy * wz, gx[1]);
+                    gx[2] = fmaf(Wbar, wxy * st.dw[2][k], gx[2]);
+                    Sv[0] = fmaf(W, g.x, Sv[0]);
+                    Sv[1] = fmaf(W, g.y, Sv[1]);
+                    Sv[2] = fmaf(W, g.z, Sv[2]);
                 }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) gx[c] -= kgC[0][c] * Sv[0] + kgC[1][c] * Sv[1] + kgC[2][c] * Sv[2];
 #pragma unroll
         for (int k = 0; k < 3; k++) A.adj[(kX + k) * N + p] = gx[k];
     }
@@ -634,42 +663,58 @@ __device__ __forceinline__ void p2g_bwd_gather(const InstDev& I, const AdjArgs& 
     node_offsets(I, st, ox, oy, oz);
     const float4* ga = A.gacc + I.node_off;
     const AxisX lx = axis_x(st, ox);
+    // Per node: a = m_p v + Am d (hoisted over the loops), Wbar = m-bar m_p +
+    // mv-bar . a, gx += Wbar grad W, gA += W mv-bar d^T. The terms of gx
+    // through d = x_node - x_p sum to -Am^T S1 with S1 = sum W mv-bar, and
+    // gv, gmp follow from S1 and S0 = sum W m-bar after the loop.
+    float S0 = 0.f, S1[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int r = 0; r < 3; r++) {
-        gv[r] = 0.f;
+    for (int r = 0; r < 3; r++)
 #pragma unroll
         for (int c = 0; c < 3; c++) gA[r][c] = 0.f;
-    }
 #pragma unroll 1
-    for (int i = 0; i < 3; i++)
+    for (int i = 0; i < 3; i++) {
+        const float wx = lx.w[i], dwx = lx.dw[i], dxi = (float(i) - st.fx[0]) * I.dx;
+        float ai[3];
 #pragma unroll
-        for (int j = 0; j < 3; j++)
+        for (int r = 0; r < 3; r++) ai[r] = fmaf(Am[r][0], dxi, I.mp * v[r]);
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float wy = st.w[1][j], dyj = (float(j) - st.fx[1]) * I.dx;
+            const float wxy = wx * wy, gwx = dwx * wy, gwy = wx * st.dw[1][j];
+            float aij[3];
+#pragma unroll
+            for (int r = 0; r < 3; r++) aij[r] = fmaf(Am[r][1], dyj, ai[r]);
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                const float wx = lx.w[i], wy = st.w[1][j], wz = st.w[2][k];
-                const float W = wx * wy * wz;
-                const float gW[3] = {lx.dw[i] * wy * wz, wx * st.dw[1][j] * wz, wx * wy * st.dw[2][k]};
-                const float d[3] = {(float(i) - st.fx[0]) * I.dx, (float(j) - st.fx[1]) * I.dx,
-                                    (float(k) - st.fx[2]) * I.dx};
+                const float wz = st.w[2][k], dzk = (float(k) - st.fx[2]) * I.dx;
+                const float W = wxy * wz;
                 const float4 g = ga[lx.o[i] + oy[j] + oz[k]];
                 const float gm = g.x, gmv[3] = {g.y, g.z, g.w};
                 float Wbar = gm * I.mp;
 #pragma unroll
+                for (int r = 0; r < 3; r++) Wbar = fmaf(gmv[r], fmaf(Am[r][2], dzk, aij[r]), Wbar);
+                gx[0] = fmaf(Wbar, gwx * wz, gx[0]);
+                gx[1] = fmaf(Wbar, gwy * wz, gx[1]);
+                gx[2] = fmaf(Wbar, wxy * st.dw[2][k], gx[2]);
+                S0 = fmaf(W, gm, S0);
+#pragma unroll
                 for (int r = 0; r < 3; r++) {
-                    const float Ad = Am[r][0] * d[0] + Am[r][1] * d[1] + Am[r][2] * d[2];
-                    Wbar += gmv[r] * (I.mp * v[r] + Ad);
-                    gv[r] += W * I.mp * gmv[r];
-                    gmp += W * gmv[r] * v[r];
-#pragma unroll
-                    for (int c = 0; c < 3; c++) gA[r][c] += W * gmv[r] * d[c];
-                }
-                gmp += W * gm;
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    const float dbar = W * (Am[0][c] * gmv[0] + Am[1][c] * gmv[1] + Am[2][c] * gmv[2]);
-                    gx[c] += Wbar * gW[c] - dbar;
+                    const float Wg = W * gmv[r];
+                    S1[r] += Wg;
+                    gA[r][0] = fmaf(Wg, dxi, gA[r][0]);
+                    gA[r][1] = fmaf(Wg, dyj, gA[r][1]);
+                    gA[r][2] = fmaf(Wg, dzk, gA[r][2]);
                 }
             }
+        }
+    }
+    gmp += S0 + S1[0] * v[0] + S1[1] * v[1] + S1[2] * v[2];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        gv[c] = I.mp * S1[c];
+        gx[c] -= Am[0][c] * S1[0] + Am[1][c] * S1[1] + Am[2][c] * S1[2];
+    }
 }
 
 // The chain through the trial F = (I + dt C) F and the stores of the
