@@ -237,7 +237,7 @@ def batched_vs_serial(n_inst: int, nsub: int, steps: int, sort_every: int):
 # --------------------------------------------------------------------------
 def auto_checkpoint(S: int, slot_state: int, slot_grid: int, free_bytes: int) -> int:
     """The largest checkpoint interval K <= S whose recorded segment (K + 1
-    states and K grids) takes at most half the free device memory: with
+    states, K grids and SVD records) takes at most half the free device memory: with
     K = S the backward reverses the recorded rollout without recomputing it."""
     budget = free_bytes // 2
     K = (budget - slot_state) // (slot_state + slot_grid)
@@ -265,7 +265,9 @@ def run_ours(args):
     w = W.cfg_1m()
     N, S = w.n, args.substeps
     nodes = int(np.prod([-(-r // 4) * 4 for r in w.res]))
-    slot_state, slot_grid = 96 * N, 32 * nodes + nodes // 64
+    # per recorded substep: a state (96 B/particle), the grids (acc + vout +
+    # flags) and the SVD of the trial F (96 B/particle)
+    slot_state, slot_grid = 96 * N, 32 * nodes + nodes // 64 + 96 * N
     K = args.checkpoint or auto_checkpoint(S, slot_state, slot_grid, torch.cuda.mem_get_info(local)[0])
     record_bytes = (K + 1) * slot_state + K * slot_grid
     stream = torch.cuda.Stream()

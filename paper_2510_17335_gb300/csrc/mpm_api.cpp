@@ -159,6 +159,7 @@ struct mpm_handle {
     std::vector<DevBuf<float>> seg_state;
     std::vector<DevBuf<float4>> seg_acc, seg_vout;
     std::vector<DevBuf<unsigned char>> seg_flags;
+    std::vector<DevBuf<float>> seg_spec;   // SVD of the trial F of substep k (k = 0..K-1)
     std::vector<char> seg_dirty;      // grid slot k holds accumulators/flags to clear
     int64_t seg_valid = -1;           // segment whose states/grids the slots hold
     int seg_valid_len = 0;
@@ -453,6 +454,7 @@ int ensure_slot(mpm_handle* h, int k) {
         h->seg_acc.resize(need - 1);
         h->seg_vout.resize(need - 1);
         h->seg_flags.resize(need - 1);
+        h->seg_spec.resize(need - 1);
         h->seg_dirty.resize(need - 1, 0);
     }
     for (size_t i = 0; i < need; i++) RK(h->seg_state[i].ensure(state_floats, h->device_bytes));
@@ -460,6 +462,7 @@ int ensure_slot(mpm_handle* h, int k) {
         RK(h->seg_acc[k].ensure((size_t)h->n_nodes, h->device_bytes));
         RK(h->seg_vout[k].ensure((size_t)h->n_nodes, h->device_bytes));
         RK(h->seg_flags[k].ensure((size_t)h->n_blocks, h->device_bytes));
+        RK(h->seg_spec[k].ensure((size_t)h->ncap * kSpecComps, h->device_bytes));
         CK(cudaMemsetAsync(h->seg_acc[k].p, 0, (size_t)h->n_nodes * sizeof(float4), h->stream));
         CK(cudaMemsetAsync(h->seg_flags[k].p, 0, (size_t)h->n_blocks, h->stream));
         h->seg_dirty[k] = 0;
@@ -475,6 +478,7 @@ StepArgs slot_args(mpm_handle* h, int k, int64_t substep) {
     a.acc = h->seg_acc[k].p;
     a.vout = h->seg_vout[k].p;
     a.flags = h->seg_flags[k].p;
+    a.spec = h->seg_spec[k].p;
     a.keep_grid = 1;
     a.substep = (int)substep;
     return a;
@@ -684,6 +688,7 @@ void mpm_destroy(mpm_handle* h) {
     for (auto& b : h->seg_acc) b.release();
     for (auto& b : h->seg_vout) b.release();
     for (auto& b : h->seg_flags) b.release();
+    for (auto& b : h->seg_spec) b.release();
     h->d_gacc.release();
     h->d_adj.release(); h->d_gmat.release(); h->d_gpose.release();
     h->d_state2.release(); h->d_adj2.release(); h->d_ext2.release(); h->d_key.release(); h->d_rank.release();

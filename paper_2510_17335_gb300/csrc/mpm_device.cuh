@@ -786,9 +786,11 @@ struct TileSmem {
     int tiled;
 };
 
-// bounding box of the stencils of the active threads' particles; all
-// threads of the CTA must call it
-__device__ __forceinline__ void tile_begin(TileSmem& T, bool active, const Stencil& st, int nthreads) {
+// bounding box of the stencils of the active threads' particles: lo and
+// dim (nodes per axis; 0 when no thread is active) are written by thread 0
+// and visible to all after the call; all threads of the CTA must call it
+__device__ __forceinline__ void stencil_bbox(bool active, const Stencil& st, int nthreads, int* lo_out,
+                                             int* dim_out) {
     int lo[3], hi[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -807,15 +809,23 @@ __device__ __forceinline__ void tile_begin(TileSmem& T, bool active, const Stenc
         for (int a = 0; a < 3; a++) { s_lo[a][warp] = lo[a]; s_hi[a][warp] = hi[a]; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int n = 1;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             int l = s_lo[a][0], h = s_hi[a][0];
             for (int w = 1; w < nw; w++) { l = min(l, s_lo[a][w]); h = max(h, s_hi[a][w]); }
-            T.lo[a] = l;
-            T.dim[a] = (h >= l) ? h - l + 3 : 0;
-            n *= T.dim[a];
+            lo_out[a] = l;
+            dim_out[a] = (h >= l) ? h - l + 3 : 0;
         }
+    }
+    __syncthreads();
+}
+
+// the CTA's scatter tile: bounding box, tiled flag, zeroed sums; all threads
+// of the CTA must call it
+__device__ __forceinline__ void tile_begin(TileSmem& T, bool active, const Stencil& st, int nthreads) {
+    stencil_bbox(active, st, nthreads, T.lo, T.dim);
+    if (threadIdx.x == 0) {
+        const int n = T.dim[0] * T.dim[1] * T.dim[2];
         T.tiled = (n > 0 && n <= kTileNodes) ? 1 : 0;
     }
     __syncthreads();

@@ -23,7 +23,7 @@
 // minimum resident CTAs per SM of the particle kernels (register caps; the
 // defaults are the fastest of a measured sweep on the 1M-particle bed)
 #ifndef MPM_MINB_P2G
-#define MPM_MINB_P2G 3
+#define MPM_MINB_P2G 4
 #endif
 #ifndef MPM_MINB_G2P
 #define MPM_MINB_G2P 4
@@ -115,6 +115,38 @@ __device__ __forceinline__ void load_trial(const InstDev& I, const StepArgs& a, 
             Ft[r][c] = F[r][c] + I.dt * (C[r][0] * F[0][c] + C[r][1] * F[1][c] + C[r][2] * F[2][c]);
 }
 
+// The recorded SVD of a particle's trial F (record mode): the adjoint
+// rebuilds the return mapping from it instead of redoing the SVD.
+__device__ __forceinline__ void store_svd(float* spec, long long N, long long p, const Spectral<float>& S) {
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            spec[(3 * r + c) * N + p] = S.U[r][c];
+            spec[(9 + 3 * r + c) * N + p] = S.V[r][c];
+        }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        spec[(18 + k) * N + p] = S.s[k];
+        spec[(21 + k) * N + p] = S.h[k];
+    }
+}
+
+__device__ __forceinline__ void load_svd(const float* spec, long long N, long long p, Spectral<float>& S) {
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            S.U[r][c] = spec[(3 * r + c) * N + p];
+            S.V[r][c] = spec[(9 + 3 * r + c) * N + p];
+        }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        S.s[k] = spec[(18 + k) * N + p];
+        S.h[k] = spec[(21 + k) * N + p];
+    }
+}
+
 // APIC + MLS stress transfer of one particle to its 27 nodes: mass m_p W and
 // momentum W (m_p v + A d), A = stress_scale tau + m_p C. Sums in the shared
 // tile when T is given and tiled, else with global atomics.
@@ -198,6 +230,7 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_P2G) k_p2g(StepArgs a) {
         load_trial(I, a, p, C, Ft);
         Spectral<float> S;
         constitutive_spectral<float>(Ft, I.mu, I.lam, I.beta, I.smin, S);
+        if (a.spec) store_svd(a.spec, N, p, S);
         if (needs_fp64(S)) {
             a.fb_list[atomicAdd(a.fb_count, 1)] = (int)p;
         } else {
@@ -307,24 +340,28 @@ __global__ void __launch_bounds__(256) k_grid(StepArgs a) {
     if (!a.keep_grid && lane == 0) a.flags[gw] = 0;
 }
 
-__global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
-    __shared__ InstDev sI;
-    const int inst = a.chunk_inst[blockIdx.x];
-    const InstDev& I = stage_instance(sI, a.inst, inst);
-    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
-    if (p - I.pbeg >= I.n) return;
-    const long long N = a.ncap;
-    float x[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) x[k] = ld(a.sin, N, kX + k, p);
-    Stencil st;
-    make_stencil(I, x, st);
+// The 27 nodes of a particle's stencil in the global grid.
+struct GlobalNodes {
+    const float4* g;      // the instance's grid
     int ox[3], oy[3], oz[3];
-    node_offsets(I, st, ox, oy, oz);
-    const float4* vg = a.vout + I.node_off;
-    // v = sum W v_node and B = sum W v_node (o - f)^T, summed over k first:
-    // T0 = sum_k wz v_node, T1 = sum_k wz (k - fz) v_node per (i, j)
-    float v[3] = {0.0f, 0.0f, 0.0f}, B[3][3] = {{0.0f}};
+    __device__ __forceinline__ GlobalNodes(const InstDev& I, const Stencil& st, const float4* grid)
+        : g(grid + I.node_off) {
+        node_offsets(I, st, ox, oy, oz);
+    }
+    __device__ __forceinline__ float4 node(int i, int j, int k) const {
+        return __ldg(g + sel3(ox, i) + oy[j] + oz[k]);
+    }
+};
+
+// v = sum W v_node and B = sum W v_node (o - f)^T, summed over k first:
+// T0 = sum_k wz v_node, T1 = sum_k wz (k - fz) v_node per (i, j)
+template <class Nodes>
+__device__ __forceinline__ void g2p_gather(const Stencil& st, const Nodes& src, float (&v)[3], float (&B)[3][3]) {
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        v[r] = 0.f;
+        B[r][0] = B[r][1] = B[r][2] = 0.f;
+    }
     float wzd[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) wzd[k] = st.w[2][k] * (float(k) - st.fx[2]);
@@ -332,14 +369,13 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
     for (int i = 0; i < 3; i++) {
         const float di = float(i) - st.fx[0];
         const float wx = sel3(st.w[0], i);
-        const int oxi = sel3(ox, i);
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             const float dj = float(j) - st.fx[1];
             float T0[3] = {0.f, 0.f, 0.f}, T1[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                const float4 g = __ldg(vg + oxi + oy[j] + oz[k]);
+                const float4 g = src.node(i, j, k);
                 const float gg[3] = {g.x, g.y, g.z};
 #pragma unroll
                 for (int r = 0; r < 3; r++) {
@@ -357,6 +393,22 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
+    __shared__ InstDev sI;
+    const int inst = a.chunk_inst[blockIdx.x];
+    const InstDev& I = stage_instance(sI, a.inst, inst);
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (p - I.pbeg >= I.n) return;
+    const long long N = a.ncap;
+    float x[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) x[k] = ld(a.sin, N, kX + k, p);
+    Stencil st;
+    make_stencil(I, x, st);
+    float v[3], B[3][3];
+    g2p_gather(st, GlobalNodes(I, st, a.vout), v, B);
     // C = 4/dx^2 sum W v d^T with d = (o - f) dx
     const float cscale = 4.0f * I.inv_dx;
     if (I.pcoll && I.shovel_on) {
@@ -394,6 +446,60 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
 // ---------------------------------------------------------------------------
 // adjoint
 // ---------------------------------------------------------------------------
+// Adjoint of the APIC gather for one particle: scatter W b into the grid
+// velocity adjoint with b = gvn + kap gC d (hoisted over the loops), and
+// gx += sum Wbar grad W; the terms of gx through d sum to -kap gC^T Sv with
+// Sv = sum W v_node (velocities of the grid vg).
+__device__ __forceinline__ void g2p_bwd_scatter(const InstDev& I, const AdjArgs& A, const Stencil& st,
+                                                const int (&ox)[3], const int (&oy)[3], const int (&oz)[3],
+                                                const float4* vg, TileSmem& T, const float (&gvn)[3],
+                                                const float (&gC)[3][3], float (&gx)[3]) {
+    const float kap = 4.0f * I.inv_dx * I.inv_dx;
+    float kgC[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) kgC[r][c] = kap * gC[r][c];
+    float Sv[3] = {0.f, 0.f, 0.f};
+    float4* ga = A.gacc + I.node_off;
+    const AxisX lx = axis_x(st, ox);
+#pragma unroll 1
+    for (int i = 0; i < 3; i++) {
+        const float wx = lx.w[i], dwx = lx.dw[i], dxi = (float(i) - st.fx[0]) * I.dx;
+        float bi[3];
+#pragma unroll
+        for (int r = 0; r < 3; r++) bi[r] = fmaf(kgC[r][0], dxi, gvn[r]);
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float wy = st.w[1][j], dyj = (float(j) - st.fx[1]) * I.dx;
+            const float wxy = wx * wy, gwx = dwx * wy, gwy = wx * st.dw[1][j];
+            float bij[3];
+#pragma unroll
+            for (int r = 0; r < 3; r++) bij[r] = fmaf(kgC[r][1], dyj, bi[r]);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float wz = st.w[2][k], dzk = (float(k) - st.fx[2]) * I.dx;
+                const float W = wxy * wz;
+                const float4 g = __ldg(vg + lx.o[i] + oy[j] + oz[k]);
+                float b[3];
+#pragma unroll
+                for (int r = 0; r < 3; r++) b[r] = fmaf(kgC[r][2], dzk, bij[r]);
+                tile_add(T, ga, lx.o[i] + oy[j] + oz[k], st, i, j, k,
+                         make_float4(W * b[0], W * b[1], W * b[2], 0.f), 3);
+                const float Wbar = g.x * b[0] + g.y * b[1] + g.z * b[2];
+                gx[0] = fmaf(Wbar, gwx * wz, gx[0]);
+                gx[1] = fmaf(Wbar, gwy * wz, gx[1]);
+                gx[2] = fmaf(Wbar, wxy * st.dw[2][k], gx[2]);
+                Sv[0] = fmaf(W, g.x, Sv[0]);
+                Sv[1] = fmaf(W, g.y, Sv[1]);
+                Sv[2] = fmaf(W, g.z, Sv[2]);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) gx[c] -= kgC[0][c] * Sv[0] + kgC[1][c] * Sv[1] + kgC[2][c] * Sv[2];
+}
+
 __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A) {
     __shared__ TileSmem T;
     __shared__ InstDev sI;
@@ -464,53 +570,7 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A)
         for (int r = 0; r < 3; r++)
 #pragma unroll
             for (int c = 0; c < 3; c++) gC[r][c] = A.adj[(kC + 3 * r + c) * N + p];
-        // adjoint of the APIC gather: scatter W b into the grid velocity
-        // adjoint with b = gvn + kap gC d (hoisted over the loops); the terms
-        // of gx through d sum to -kap gC^T Sv with Sv = sum W v_node
-        const float kap = 4.0f * I.inv_dx * I.inv_dx;
-        float kgC[3][3];
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) kgC[r][c] = kap * gC[r][c];
-        float Sv[3] = {0.f, 0.f, 0.f};
-        float4* ga = A.gacc + I.node_off;
-        const AxisX lx = axis_x(st, ox);
-#pragma unroll 1
-        for (int i = 0; i < 3; i++) {
-            const float wx = lx.w[i], dwx = lx.dw[i], dxi = (float(i) - st.fx[0]) * I.dx;
-            float bi[3];
-#pragma unroll
-            for (int r = 0; r < 3; r++) bi[r] = fmaf(kgC[r][0], dxi, gvn[r]);
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                const float wy = st.w[1][j], dyj = (float(j) - st.fx[1]) * I.dx;
-                const float wxy = wx * wy, gwx = dwx * wy, gwy = wx * st.dw[1][j];
-                float bij[3];
-#pragma unroll
-                for (int r = 0; r < 3; r++) bij[r] = fmaf(kgC[r][1], dyj, bi[r]);
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    const float wz = st.w[2][k], dzk = (float(k) - st.fx[2]) * I.dx;
-                    const float W = wxy * wz;
-                    const float4 g = __ldg(vg + lx.o[i] + oy[j] + oz[k]);
-                    float b[3];
-#pragma unroll
-                    for (int r = 0; r < 3; r++) b[r] = fmaf(kgC[r][2], dzk, bij[r]);
-                    tile_add(T, ga, lx.o[i] + oy[j] + oz[k], st, i, j, k,
-                             make_float4(W * b[0], W * b[1], W * b[2], 0.f), 3);
-                    const float Wbar = g.x * b[0] + g.y * b[1] + g.z * b[2];
-                    gx[0] = fmaf(Wbar, gwx * wz, gx[0]);
-                    gx[1] = fmaf(Wbar, gwy * wz, gx[1]);
-                    gx[2] = fmaf(Wbar, wxy * st.dw[2][k], gx[2]);
-                    Sv[0] = fmaf(W, g.x, Sv[0]);
-                    Sv[1] = fmaf(W, g.y, Sv[1]);
-                    Sv[2] = fmaf(W, g.z, Sv[2]);
-                }
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < 3; c++) gx[c] -= kgC[0][c] * Sv[0] + kgC[1][c] * Sv[1] + kgC[2][c] * Sv[2];
+        g2p_bwd_scatter(I, A, st, ox, oy, oz, vg, T, gvn, gC, gx);
 #pragma unroll
         for (int k = 0; k < 3; k++) A.adj[(kX + k) * N + p] = gx[k];
     }
@@ -798,15 +858,15 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd(AdjArgs A)
             v[k] = ld(a.sin, N, kV + k, p);
             gx[k] = A.adj[(kX + k) * N + p];
         }
-        // forward constitutive step again: the stress for the gather, the
-        // spectral data for the adjoint (parked in shared memory meanwhile)
+        // the forward's SVD of the trial F (recorded) and its return mapping
+        // again: the stress for the gather, the spectral data for the adjoint
+        // (parked in shared memory meanwhile)
         bool fb;
         float Am[3][3];
         {
-            float C[3][3], Ft[3][3];
-            load_trial(I, a, p, C, Ft);
             Spectral<float> S;
-            constitutive_spectral<float>(Ft, I.mu, I.lam, I.beta, I.smin, S);
+            load_svd(a.spec, N, p, S);
+            return_map<float>(S, I.mu, I.lam, I.beta, I.smin);
             fb = needs_fp64(S);
             float Fn[3][3], tau[3][3];
             spectral_outputs<float, float>(S, Fn, tau);
@@ -814,7 +874,7 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd(AdjArgs A)
 #pragma unroll
             for (int r = 0; r < 3; r++)
 #pragma unroll
-                for (int c = 0; c < 3; c++) Am[r][c] = I.stress_scale * tau[r][c] + I.mp * C[r][c];
+                for (int c = 0; c < 3; c++) Am[r][c] = I.stress_scale * tau[r][c] + I.mp * ld(a.sin, N, kC + 3 * r + c, p);
         }
         if (fb) {
             a.fb_list[atomicAdd(a.fb_count, 1)] = (int)p;
@@ -1140,7 +1200,10 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
         case KernelId::G2P: k_g2p<<<a.n_chunks, kChunk, 0, s>>>(a); break;
         case KernelId::G2PBwd: k_g2p_bwd<<<a.n_chunks, kChunk, 0, s>>>(A); break;
         case KernelId::GridBwd: k_grid_bwd<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
-        case KernelId::P2GBwd: k_p2g_bwd<<<a.n_chunks, kChunk, 0, s>>>(A); break;
+        case KernelId::P2GBwd:
+            if (!a.spec) return cudaErrorInvalidValue;   // needs the recorded SVD
+            k_p2g_bwd<<<a.n_chunks, kChunk, 0, s>>>(A);
+            break;
         case KernelId::GridClear: k_grid_clear<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
         case KernelId::P2GFp64: k_p2g_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(a); break;
         case KernelId::P2GBwdFp64: k_p2g_bwd_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(A); break;

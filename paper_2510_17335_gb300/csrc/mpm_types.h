@@ -7,6 +7,7 @@ namespace mpm {
 constexpr int kChunk = 256;        // particles per CTA in particle kernels; instances are padded to it
 constexpr int kStateComps = 24;    // x 3, v 3, C 9, F 9 (structure of arrays)
 constexpr int kX = 0, kV = 3, kC = 6, kF = 15;
+constexpr int kSpecComps = 24;     // recorded SVD of the trial F: U 9, V 9, sigma 3, sigma^2 - 1 3
 
 // status bits written by kernels
 constexpr int kStatusDomain = 1;
@@ -55,6 +56,8 @@ struct StepArgs {
     unsigned long long* fp64_count;
     float clip;             // > 0: clip adjoints to [-clip, clip]
     int tile;               // 1: sum scatters in a shared-memory tile per CTA
+    float* spec;            // record mode: SVD of the trial F per particle [kSpecComps][ncap]
+                            // (U row-major, V row-major, sigma, sigma^2 - 1), else null
     int* fb_list;           // particles deferred to the FP64 constitutive kernels [ncap]
     int* fb_count;          // [0] entries of fb_list, [1] CTA ticket; both zero between launches
 };
