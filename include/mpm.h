@@ -91,6 +91,8 @@ typedef struct {
     double sigma_min;         /* [1e-4] singular values are clamped here before the log */
     int sort_every;           /* [0] reorder particles by grid block every n substeps (0: never) */
     int tile_scatter;         /* [0] sum the 27-node scatters in shared-memory tiles per CTA */
+    int cuda_graphs;          /* [1] replay repeated identical mpm_forward / mpm_backward calls
+                               * from CUDA graphs (see below) */
 } mpm_options;
 
 /* Digging skill (Sec. III-B): theta = (displace, rotate, insert_dist,
@@ -112,6 +114,7 @@ typedef struct {
     int64_t device_bytes;     /* device memory held */
     int64_t kernel_launches;  /* kernels launched by the library so far */
     int64_t fp64_fallbacks;   /* constitutive evaluations redone in FP64 */
+    int64_t graph_launches;   /* forward / backward calls replayed from CUDA graphs */
 } mpm_info_t;
 
 /* Create a batch of n_inst independent instances. cfgs/mats have n_inst
@@ -154,6 +157,19 @@ int mpm_get_state(mpm_handle* h, float* x, float* v, float* C, float* F, int dev
  * checkpoints). A recording forward continues an existing record only if
  * the previous call recorded too. */
 int mpm_forward(mpm_handle* h, int n_substeps, int record);
+
+/* CUDA graphs (option cuda_graphs, on by default). An optimisation loop runs
+ * the same rollout again and again: set the state (and material or skill),
+ * mpm_forward(n, 1), a loss, mpm_backward. Such a call issues exactly the
+ * launches of the previous identical call: same n, record flag, substep and
+ * record position, and the same segment bookkeeping. The second time a call
+ * is seen the library captures its launches into a CUDA graph; from the
+ * third time on it replays that graph with one cudaGraphLaunch. Material,
+ * skill, state and loss seeds live in device buffers the graph reads, so
+ * they may change between replays. Replay gives results identical to eager
+ * launches. No graph is used while profiling or sorting, and a capture
+ * that fails (for example because it would allocate) falls back to eager
+ * launches. Up to 16 graphs are kept per handle. */
 
 /* L_i = (1/N_i) sum_p |x_p - xhat_p|^2 per instance (FP64 accumulation) and,
  * if dL_dx != NULL, dL/dx = 2 (x - xhat) / N_i (external order). */

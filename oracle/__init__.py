@@ -120,6 +120,26 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
+class _ObsGrid(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_double), ("cz", ctypes.c_double), ("size", ctypes.c_double), ("res", ctypes.c_int),
+                ("tap", ctypes.c_double)]
+
+
+@dataclass
+class ObsGrid:
+    """Observation / height-map square (Sec. III-A): res x res pixels of
+    side size in the (x, z) plane, centred at (cx, cz); tap is the splat
+    offset of the height map."""
+    cx: float
+    cz: float
+    size: float = 0.24
+    res: int = 40
+    tap: float = 0.0
+
+    def c(self):
+        return _ObsGrid(self.cx, self.cz, self.size, self.res, self.tap)
+
+
 def _declare(L):
     P = ctypes.POINTER(_Params)
     i64 = ctypes.c_int64
@@ -142,6 +162,14 @@ def _declare(L):
     L.orc_skill_actions.restype = ctypes.c_int
     L.orc_pose_table.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]
     L.orc_pose_table_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
+    G = ctypes.POINTER(_ObsGrid)
+    _fp = ctypes.POINTER(ctypes.c_float)
+    _i64p = ctypes.POINTER(ctypes.c_int64)
+    L.orc_surface_observation.argtypes = [G, i64, _fp, _i64p]
+    L.orc_surface_observation.restype = ctypes.c_int
+    L.orc_height_map.argtypes = [G, i64, _fp, _dp, _i64p]
+    L.orc_hmd.argtypes = [G, i64, _fp, _dp, _dp]
+    L.orc_hmd.restype = ctypes.c_double
 
 
 def _d(a: np.ndarray):
@@ -278,3 +306,39 @@ def mse_loss(x, target) -> tuple[float, np.ndarray]:
     n = x.shape[0]
     d = x - t
     return float((d * d).sum() / n), 2.0 * d / n
+
+
+def _f32pts(x):
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1, 3))
+    return x, x.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def surface_observation(g: ObsGrid, x) -> tuple[int, np.ndarray]:
+    """(non-empty pixels, per-pixel index of the highest particle or -1)."""
+    x, xp = _f32pts(x)
+    idx = np.empty(g.res * g.res, np.int64)
+    gc = g.c()
+    cnt = _L().orc_surface_observation(ctypes.byref(gc), x.shape[0], xp,
+                                       idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return int(cnt), idx
+
+
+def height_map(g: ObsGrid, x) -> tuple[np.ndarray, np.ndarray]:
+    """(height map [res, res], winner particle per pixel or -1)."""
+    x, xp = _f32pts(x)
+    I = np.empty(g.res * g.res, np.float64)
+    w = np.empty(g.res * g.res, np.int64)
+    gc = g.c()
+    _L().orc_height_map(ctypes.byref(gc), x.shape[0], xp, _d(I), w.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return I.reshape(g.res, g.res), w.reshape(g.res, g.res)
+
+
+def hmd(g: ObsGrid, x, Ihat) -> tuple[float, np.ndarray]:
+    """(d_HMD, dL/dx [n, 3])."""
+    x, xp = _f32pts(x)
+    Ih = np.ascontiguousarray(np.asarray(Ihat, np.float64).reshape(-1))
+    assert Ih.size == g.res * g.res
+    grad = np.empty((x.shape[0], 3), np.float64)
+    gc = g.c()
+    L = _L().orc_hmd(ctypes.byref(gc), x.shape[0], xp, _d(Ih), _d(grad))
+    return float(L), grad

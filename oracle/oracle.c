@@ -2,7 +2,8 @@
  * FP64 CPU oracle: MLS-MPM substep for sand/soil (DDBot, arXiv 2510.17335,
  * Sec. III-A, Algorithm 1, Eqs. (3)-(7)) and its reverse-mode adjoint
  * (Sec. III-D, Appendix B), plus the skill-to-action mapping (Sec. III-B,
- * Algorithm 2) and its Jacobian (Appendix A, rounded phase lengths).
+ * Algorithm 2) and its Jacobian (Appendix A, rounded phase lengths), and
+ * the surface observation and height-map distance of Sec. III-A (Eq. (2)).
  *
  * TEST INFRASTRUCTURE ONLY: plain, slow, written for a reader to check it
  * against the paper. Only tests, the smoke check and the benchmark's CPU
@@ -1015,4 +1016,70 @@ void orc_pose_table_adjoint(int n_actions, int substeps_per_action, double dt_su
         for (int k = 0; k < 4; k++)
             gactions[6 * t + k] += (suffix[k] + gposes[8 * s + 4 + k] / dt_sub) / substeps_per_action;
     }
+}
+
+/* ---------------------------------------------------------------------
+ * Surface observation, height map and HMD (Sec. III-A; Eq. (2))
+ * ------------------------------------------------------------------- */
+
+/* the pixel of an FP32 point (x, z) or -1 outside the square */
+static int64_t obs_pixel(const orc_obs_grid* g, float xf, float zf) {
+    const float x0 = (float)(g->cx - 0.5 * g->size), z0 = (float)(g->cz - 0.5 * g->size);
+    const float h = (float)(g->size / g->res);
+    const float fi = floorf((xf - x0) / h), fj = floorf((zf - z0) / h);
+    if (!(fi >= 0.0f && fi < (float)g->res && fj >= 0.0f && fj < (float)g->res)) return -1;
+    return (int64_t)fi * g->res + (int64_t)fj;
+}
+
+int orc_surface_observation(const orc_obs_grid* g, int64_t n, const float* x, int64_t* idx) {
+    const int64_t np = (int64_t)g->res * g->res;
+    for (int64_t p = 0; p < np; p++) idx[p] = -1;
+    for (int64_t q = 0; q < n; q++) {
+        const int64_t p = obs_pixel(g, x[3 * q], x[3 * q + 2]);
+        if (p < 0) continue;
+        /* strictly higher replaces: the lowest index keeps a tie */
+        if (idx[p] < 0 || x[3 * q + 1] > x[3 * idx[p] + 1]) idx[p] = q;
+    }
+    int count = 0;
+    for (int64_t p = 0; p < np; p++) count += idx[p] >= 0;
+    return count;
+}
+
+void orc_height_map(const orc_obs_grid* g, int64_t n, const float* x, double* I, int64_t* winner) {
+    const int64_t np = (int64_t)g->res * g->res;
+    for (int64_t p = 0; p < np; p++) {
+        I[p] = 0.0;
+        winner[p] = -1;
+    }
+    const float r = (float)g->tap;
+    for (int64_t q = 0; q < n; q++) {
+        const float xf = x[3 * q], yf = x[3 * q + 1], zf = x[3 * q + 2];
+        const float tx[5] = {xf, xf + r, xf - r, xf, xf};
+        const float tz[5] = {zf, zf, zf, zf + r, zf - r};
+        for (int t = 0; t < 5; t++) {
+            const int64_t p = obs_pixel(g, tx[t], tz[t]);
+            if (p < 0) continue;
+            if ((double)yf > I[p]) {
+                I[p] = (double)yf;
+                winner[p] = q;
+            }
+        }
+    }
+}
+
+double orc_hmd(const orc_obs_grid* g, int64_t n, const float* x, const double* Ihat, double* dL_dx) {
+    const int64_t np = (int64_t)g->res * g->res;
+    double* I = (double*)malloc((size_t)np * sizeof(double));
+    int64_t* w = (int64_t*)malloc((size_t)np * sizeof(int64_t));
+    orc_height_map(g, n, x, I, w);
+    if (dL_dx) memset(dL_dx, 0, (size_t)n * 3 * sizeof(double));
+    double L = 0.0;
+    for (int64_t p = 0; p < np; p++) {
+        const double d = I[p] - Ihat[p];
+        L += fabs(d);
+        if (dL_dx && w[p] >= 0) dL_dx[3 * w[p] + 1] += (d > 0.0) - (d < 0.0);
+    }
+    free(I);
+    free(w);
+    return L;
 }

@@ -104,4 +104,41 @@ void orc_pose_table(const double start[4], int n_actions, const double* actions,
 void orc_pose_table_adjoint(int n_actions, int substeps_per_action, double dt_sub, int nsub,
                             const double* gposes, double* gactions);
 
+/* ---------------------------------------------------------------------
+ * Surface observation and height-map distance (Sec. III-A, "States and
+ * observations" and Eq. (2) of "Goal and reward/loss").
+ *
+ * A res x res square of pixels of side `size` lies in the horizontal (x, z)
+ * plane (y is up), centred at (cx, cz). Pixel (i, j) of a point holds
+ *   i = floorf((xf - x0f) / hf),  j = floorf((zf - z0f) / hf)
+ * in FP32 arithmetic, with x0f = (float)(cx - size/2), z0f = (float)(cz -
+ * size/2), hf = (float)(size/res); points outside [0, res)^2 are skipped.
+ * Pixel p = i * res + j. Particle positions are FP32 (the simulator's
+ * state); every selection compares FP32 heights, so the GPU can be checked
+ * index for index.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    double cx, cz;      /* centre of the square (x, z) */
+    double size;        /* side (0.24 m in the paper) */
+    int res;            /* pixels per side (40) */
+    double tap;         /* height-map splat offset r_p (m) */
+} orc_obs_grid;
+
+/* Surface observation: per pixel the highest particle (largest y; equal
+ * heights: the lowest particle index). idx[p] = that particle or -1.
+ * Returns the number of non-empty pixels. */
+int orc_surface_observation(const orc_obs_grid* g, int64_t n, const float* x, int64_t* idx);
+
+/* Height map: each particle covers the pixels of (x, z), (x + r, z),
+ * (x - r, z), (x, z + r), (x, z - r), r = (float)tap, FP32 sums. I starts at
+ * zero and a pixel takes a covering particle's y when it is higher than the
+ * current value, particles in index order (so equal heights keep the lowest
+ * index). winner[p] = the particle whose y the pixel holds, or -1. */
+void orc_height_map(const orc_obs_grid* g, int64_t n, const float* x, double* I, int64_t* winner);
+
+/* d_HMD = sum_p |I_p - Ihat_p| and, if dL_dx != NULL, its gradient w.r.t.
+ * the particle positions: dL/dy of a particle = the sum of sign(I_p - Ihat_p)
+ * over the pixels it wins (0 for x and z, and sign(0) = 0). */
+double orc_hmd(const orc_obs_grid* g, int64_t n, const float* x, const double* Ihat, double* dL_dx);
+
 #endif

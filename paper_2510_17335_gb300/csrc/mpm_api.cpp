@@ -176,6 +176,52 @@ struct mpm_handle {
     std::vector<char> seg_sorted;
     int64_t since_sort = 1LL << 40;
     Profiler prof;
+    // CUDA graphs of repeated identical forward / backward calls
+    std::vector<struct GraphEntry*> graphs;
+    int64_t graph_tick = 0;
+    int64_t graph_launches = 0;
+};
+
+// The host bookkeeping a forward or backward call reads and changes: two
+// calls that start from equal snapshots (with the same arguments) issue the
+// same launches and end in equal snapshots.
+struct HostSnap {
+    int64_t substep = 0, rec_start = 0, rec_len = 0, seg_valid = -1, since_sort = 0;
+    int seg_valid_len = 0, tile = 0;
+    bool recording = false, gacc_dirty = false;
+    std::vector<char> seg_dirty, seg_sorted;
+    // equal as far as the launches go: flags compare as if padded with
+    // zeros, and the record position does not matter while not recording
+    // (a recording forward starts a new record then)
+    static bool same_flags(const std::vector<char>& a, const std::vector<char>& b) {
+        const size_t n = std::max(a.size(), b.size());
+        for (size_t i = 0; i < n; i++)
+            if ((i < a.size() ? a[i] : 0) != (i < b.size() ? b[i] : 0)) return false;
+        return true;
+    }
+    bool operator==(const HostSnap& o) const {
+        if (recording != o.recording) return false;
+        if (recording && (rec_start != o.rec_start || rec_len != o.rec_len)) return false;
+        return substep == o.substep && seg_valid == o.seg_valid && since_sort == o.since_sort &&
+               seg_valid_len == o.seg_valid_len && tile == o.tile && gacc_dirty == o.gacc_dirty &&
+               same_flags(seg_dirty, o.seg_dirty) && same_flags(seg_sorted, o.seg_sorted);
+    }
+};
+
+namespace {
+void drop_graphs(mpm_handle* h);
+}
+
+struct GraphEntry {
+    int kind = 0;            // 0 forward, 1 backward
+    int64_t n = 0;           // substeps (forward)
+    int flags = 0;           // record (forward) / seeds present (backward)
+    HostSnap start, end;
+    int64_t launches = 0;    // kernels in the graph
+    int64_t used = 0;        // last use (eviction)
+    bool capturable = true;
+    int64_t alloc_bytes = 0; // device memory held at capture: any reallocation since voids the graph
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -599,6 +645,7 @@ int mpm_create(int n_inst, const mpm_config* cfgs, const mpm_material* mats, con
     h->opt.sigma_min = 1e-4;
     h->opt.sort_every = 0;
     h->opt.tile_scatter = 0;
+    h->opt.cuda_graphs = 1;
     if (opts) h->opt = *opts;
     h->tile_scatter = h->opt.tile_scatter ? 1 : 0;
     h->n_ext = n_ext;
@@ -679,6 +726,7 @@ void mpm_destroy(mpm_handle* h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
     h->d_inst.release(); h->d_chunk_inst.release(); h->d_block_inst.release(); h->d_ext_of_slot.release();
     h->d_state.release(); h->d_x0.release(); h->d_stage.release(); h->d_poses.release(); h->d_target.release();
     h->d_acc.release(); h->d_vout.release(); h->d_flags.release(); h->d_status.release(); h->d_fp64.release();
@@ -837,9 +885,138 @@ int mpm_get_state(mpm_handle* h, float* x, float* v, float* C, float* F, int dev
     return MPM_OK;
 }
 
-int mpm_forward(mpm_handle* h, int n_substeps, int record) {
-    if (!h || n_substeps < 0) return MPM_ERR_INVALID_ARG;
-    RK(set_device(h));
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// CUDA graphs of repeated identical calls
+// ---------------------------------------------------------------------------
+namespace {
+
+HostSnap snap(const mpm_handle* h) {
+    HostSnap s;
+    s.substep = h->substep;
+    s.rec_start = h->rec_start;
+    s.rec_len = h->rec_len;
+    s.seg_valid = h->seg_valid;
+    s.since_sort = h->since_sort;
+    s.seg_valid_len = h->seg_valid_len;
+    s.tile = h->tile_scatter;
+    s.recording = h->recording;
+    s.gacc_dirty = h->gacc_dirty;
+    s.seg_dirty = h->seg_dirty;
+    s.seg_sorted = h->seg_sorted;
+    return s;
+}
+
+void restore(mpm_handle* h, const HostSnap& s) {
+    h->substep = s.substep;
+    h->rec_start = s.rec_start;
+    h->rec_len = s.rec_len;
+    h->seg_valid = s.seg_valid;
+    h->since_sort = s.since_sort;
+    h->seg_valid_len = s.seg_valid_len;
+    h->tile_scatter = s.tile;
+    h->recording = s.recording;
+    h->gacc_dirty = s.gacc_dirty;
+    h->seg_dirty = s.seg_dirty;
+    h->seg_sorted = s.seg_sorted;
+}
+
+void drop_graphs(mpm_handle* h) {
+    for (GraphEntry* e : h->graphs) {
+        if (e->exec) cudaGraphExecDestroy(e->exec);
+        delete e;
+    }
+    h->graphs.clear();
+}
+
+constexpr size_t kMaxGraphs = 16;
+
+// Run `launch` (kernel launches and host bookkeeping only: no allocation, no
+// synchronisation) eagerly, or capture it, or replay its graph.
+template <class F>
+int run_graphed(mpm_handle* h, int kind, int64_t n, int flags, F&& launch) {
+    if (!h->opt.cuda_graphs || h->prof.on || h->opt.sort_every > 0) return launch();
+    const HostSnap start = snap(h);
+    GraphEntry* e = nullptr;
+    for (GraphEntry* g : h->graphs)
+        if (g->kind == kind && g->n == n && g->flags == flags && g->start == start) e = g;
+    if (e && e->alloc_bytes != h->device_bytes) {
+        // a buffer was reallocated since: the graph may hold stale pointers
+        if (e->exec) cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+        e->capturable = true;
+        e->alloc_bytes = -1;
+    }
+    if (!e || e->alloc_bytes < 0) {
+        // first time (with this memory): run eagerly, it may allocate
+        if (!e) {
+            if (h->graphs.size() >= kMaxGraphs) {
+                auto old = std::min_element(h->graphs.begin(), h->graphs.end(), [](const GraphEntry* a,
+                                                                                   const GraphEntry* b) {
+                    return a->used < b->used;
+                });
+                if ((*old)->exec) cudaGraphExecDestroy((*old)->exec);
+                delete *old;
+                h->graphs.erase(old);
+            }
+            e = new GraphEntry();
+            e->kind = kind;
+            e->n = n;
+            e->flags = flags;
+            e->start = start;
+            h->graphs.push_back(e);
+        }
+        e->used = ++h->graph_tick;
+        e->alloc_bytes = -1;
+        const int rc = launch();
+        if (rc == MPM_OK) e->alloc_bytes = h->device_bytes;
+        return rc;
+    }
+    e->used = ++h->graph_tick;
+    if (e->exec) {
+        CK(cudaGraphLaunch(e->exec, h->stream));
+        h->graph_launches++;
+        restore(h, e->end);
+        h->launches += e->launches;
+        return MPM_OK;
+    }
+    if (!e->capturable) return launch();
+    // second time: capture the launches, then launch the graph
+    const int64_t l0 = h->launches;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        e->capturable = false;
+        return launch();
+    }
+    const int rc = launch();
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+    cudaGraphExec_t x = nullptr;
+    bool ok = rc == MPM_OK && ce == cudaSuccess && g != nullptr && h->device_bytes == e->alloc_bytes;
+    if (ok && cudaGraphInstantiate(&x, g, 0) != cudaSuccess) ok = false;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        // nothing of the captured work ran: undo the bookkeeping, run eagerly
+        cudaGetLastError();
+        if (x) cudaGraphExecDestroy(x);
+        restore(h, start);
+        h->launches = l0;
+        e->capturable = false;
+        return launch();
+    }
+    e->end = snap(h);
+    e->launches = h->launches - l0;
+    e->exec = x;
+    CK(cudaGraphLaunch(x, h->stream));
+    h->graph_launches++;
+    return MPM_OK;
+}
+
+}  // namespace
+
+// The launches of mpm_forward and their bookkeeping (no synchronisation).
+static int forward_launch(mpm_handle* h, int n_substeps, int record) {
     const int K = h->opt.checkpoint_every;
     if (record) {
         if (!h->recording) {
@@ -849,7 +1026,6 @@ int mpm_forward(mpm_handle* h, int n_substeps, int record) {
         }
     } else {
         h->recording = false;
-    h->seg_valid = -1;
         h->rec_len = 0;
         h->seg_valid = -1;
     }
@@ -917,66 +1093,23 @@ int mpm_forward(mpm_handle* h, int n_substeps, int record) {
         }
         RK(copy_state(h, h->d_state.p, cur));
     }
-    const int st = read_status(h);
-    if (st != MPM_OK) {
-        h->recording = false;
-        h->seg_valid = -1;
-    }
-    return st;
-}
-
-int mpm_loss_mse(mpm_handle* h, const float* x_target, double* loss, float* dL_dx, int device_ptrs) {
-    if (!h || !x_target || !loss) return MPM_ERR_INVALID_ARG;
-    RK(set_device(h));
-    const size_t n = (size_t)h->n_ext;
-    const float* tgt = x_target;
-    float* out = dL_dx;
-    if (!device_ptrs) {
-        RK(h->d_target.ensure(std::max<size_t>(n, 1) * 6, h->device_bytes));
-        CK(cudaMemcpyAsync(h->d_target.p, x_target, n * 3 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
-        tgt = h->d_target.p;
-        out = dL_dx ? h->d_target.p + 3 * n : nullptr;
-    }
-    CK(cudaMemsetAsync(h->d_loss.p, 0, h->inst.size() * sizeof(double), h->stream));
-    CK(launch_loss_mse(h->d_inst.p, h->d_chunk_inst.p, h->n_chunks, h->ncap, h->d_ext_of_slot.p, h->d_state.p, tgt, out,
-                       h->d_loss.p, h->stream));
-    h->launches++;
-    CK(cudaMemcpyAsync(loss, h->d_loss.p, h->inst.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    if (!device_ptrs && dL_dx)
-        CK(cudaMemcpyAsync(dL_dx, out, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
     return MPM_OK;
 }
 
-int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, int device_ptrs, double* dL_dmaterial,
-                 double* dL_dtheta) {
-    if (!h) return MPM_ERR_INVALID_ARG;
-    if (!h->recording || h->rec_len == 0) return MPM_ERR_NO_RECORD;
-    RK(set_device(h));
+// The launches of mpm_backward and their bookkeeping (no synchronisation):
+// seeds gx, gv (device, external order, may be NULL) -> adjoints, parameter
+// and pose sums on the device.
+static int backward_launch(mpm_handle* h, const float* gx, const float* gv, bool fresh_gacc) {
     const int K = h->opt.checkpoint_every;
     const int n_inst = (int)h->inst.size();
     const size_t state_floats = (size_t)h->ncap * kStateComps;
-    const bool fresh_gacc = h->d_gacc.n < (size_t)h->n_nodes;
-    RK(h->d_gacc.ensure((size_t)h->n_nodes, h->device_bytes));
-    RK(h->d_adj.ensure(state_floats, h->device_bytes));
-    RK(h->d_gmat.ensure((size_t)n_inst * 4, h->device_bytes));
-    RK(h->d_gpose.ensure((size_t)h->rec_len * n_inst * 8, h->device_bytes));
     cudaStream_t s = h->stream;
     if (fresh_gacc || h->gacc_dirty) CK(cudaMemsetAsync(h->d_gacc.p, 0, h->d_gacc.n * sizeof(float4), s));
     h->gacc_dirty = true;   // until every reversed substep has cleared its blocks
-    // seed the adjoint of the final state
-    const float *gx = dL_dx, *gv = dL_dv;
-    if (!device_ptrs && (dL_dx || dL_dv)) {
-        RK(ensure_stage(h));
-        const size_t n = (size_t)h->n_ext;
-        if (dL_dx) { CK(cudaMemcpyAsync(h->d_stage.p, dL_dx, n * 3 * sizeof(float), cudaMemcpyHostToDevice, s)); gx = h->d_stage.p; }
-        if (dL_dv) { CK(cudaMemcpyAsync(h->d_stage.p + 3 * n, dL_dv, n * 3 * sizeof(float), cudaMemcpyHostToDevice, s)); gv = h->d_stage.p + 3 * n; }
-    }
     CK(launch_adj_from_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, gx, gv, h->d_adj.p, s));
     h->launches++;
     CK(cudaMemsetAsync(h->d_gmat.p, 0, (size_t)n_inst * 4 * sizeof(double), s));
     CK(cudaMemsetAsync(h->d_gpose.p, 0, (size_t)h->rec_len * n_inst * 8 * sizeof(double), s));
-
     const int64_t n_seg = (h->rec_len + K - 1) / K;
     for (int64_t j = n_seg - 1; j >= 0; j--) {
         const int64_t seg_begin = j * K;
@@ -1013,6 +1146,71 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, int devi
         }
     }
     h->gacc_dirty = false;
+    return MPM_OK;
+}
+
+extern "C" {
+
+int mpm_forward(mpm_handle* h, int n_substeps, int record) {
+    if (!h || n_substeps < 0) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    RK(run_graphed(h, 0, n_substeps, record ? 1 : 0, [&] { return forward_launch(h, n_substeps, record); }));
+    const int st = read_status(h);
+    if (st != MPM_OK) {
+        h->recording = false;
+        h->seg_valid = -1;
+    }
+    return st;
+}
+
+int mpm_loss_mse(mpm_handle* h, const float* x_target, double* loss, float* dL_dx, int device_ptrs) {
+    if (!h || !x_target || !loss) return MPM_ERR_INVALID_ARG;
+    RK(set_device(h));
+    const size_t n = (size_t)h->n_ext;
+    const float* tgt = x_target;
+    float* out = dL_dx;
+    if (!device_ptrs) {
+        RK(h->d_target.ensure(std::max<size_t>(n, 1) * 6, h->device_bytes));
+        CK(cudaMemcpyAsync(h->d_target.p, x_target, n * 3 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        tgt = h->d_target.p;
+        out = dL_dx ? h->d_target.p + 3 * n : nullptr;
+    }
+    CK(cudaMemsetAsync(h->d_loss.p, 0, h->inst.size() * sizeof(double), h->stream));
+    CK(launch_loss_mse(h->d_inst.p, h->d_chunk_inst.p, h->n_chunks, h->ncap, h->d_ext_of_slot.p, h->d_state.p, tgt, out,
+                       h->d_loss.p, h->stream));
+    h->launches++;
+    CK(cudaMemcpyAsync(loss, h->d_loss.p, h->inst.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (!device_ptrs && dL_dx)
+        CK(cudaMemcpyAsync(dL_dx, out, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPM_OK;
+}
+
+int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, int device_ptrs, double* dL_dmaterial,
+                 double* dL_dtheta) {
+    if (!h) return MPM_ERR_INVALID_ARG;
+    if (!h->recording || h->rec_len == 0) return MPM_ERR_NO_RECORD;
+    RK(set_device(h));
+    const int n_inst = (int)h->inst.size();
+    const size_t state_floats = (size_t)h->ncap * kStateComps;
+    const bool fresh_gacc = h->d_gacc.n < (size_t)h->n_nodes;
+    RK(h->d_gacc.ensure((size_t)h->n_nodes, h->device_bytes));
+    RK(h->d_adj.ensure(state_floats, h->device_bytes));
+    RK(h->d_gmat.ensure((size_t)n_inst * 4, h->device_bytes));
+    RK(h->d_gpose.ensure((size_t)h->rec_len * n_inst * 8, h->device_bytes));
+    cudaStream_t s = h->stream;
+    // seed the adjoint of the final state from library-owned copies, so
+    // that a replayed graph never holds a caller's pointer
+    const float *gx = nullptr, *gv = nullptr;
+    if (dL_dx || dL_dv) {
+        RK(ensure_stage(h));
+        const size_t n = (size_t)h->n_ext;
+        const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (dL_dx && n) { CK(cudaMemcpyAsync(h->d_stage.p, dL_dx, n * 3 * sizeof(float), kind, s)); gx = h->d_stage.p; }
+        if (dL_dv && n) { CK(cudaMemcpyAsync(h->d_stage.p + 3 * n, dL_dv, n * 3 * sizeof(float), kind, s)); gv = h->d_stage.p + 3 * n; }
+    }
+    const int flags = (gx ? 1 : 0) | (gv ? 2 : 0);
+    RK(run_graphed(h, 1, 0, flags, [&] { return backward_launch(h, gx, gv, fresh_gacc); }));
     std::vector<double> gm((size_t)n_inst * 4), gp((size_t)h->rec_len * n_inst * 8);
     CK(cudaMemcpyAsync(gm.data(), h->d_gmat.p, gm.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(gp.data(), h->d_gpose.p, gp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1250,6 +1448,7 @@ int mpm_get_info(mpm_handle* h, mpm_info_t* out) {
     out->device_bytes = h->device_bytes;
     out->kernel_launches = h->launches;
     out->fp64_fallbacks = (int64_t)fb;
+    out->graph_launches = h->graph_launches;
     return MPM_OK;
 }
 

@@ -48,7 +48,8 @@ class mpm_config(ctypes.Structure):
 
 class mpm_options(ctypes.Structure):
     _fields_ = [("checkpoint_every", ctypes.c_int), ("clip_grads", ctypes.c_int), ("clip_value", ctypes.c_double),
-                ("sigma_min", ctypes.c_double), ("sort_every", ctypes.c_int), ("tile_scatter", ctypes.c_int)]
+                ("sigma_min", ctypes.c_double), ("sort_every", ctypes.c_int), ("tile_scatter", ctypes.c_int),
+                ("cuda_graphs", ctypes.c_int)]
 
 
 class mpm_skill(ctypes.Structure):
@@ -59,7 +60,7 @@ class mpm_skill(ctypes.Structure):
 class mpm_info_t(ctypes.Structure):
     _fields_ = [("n_inst", ctypes.c_int), ("n_particles", ctypes.c_int64), ("substep", ctypes.c_int64),
                 ("recorded", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("fp64_fallbacks", ctypes.c_int64)]
+                ("fp64_fallbacks", ctypes.c_int64), ("graph_launches", ctypes.c_int64)]
 
 
 _vp, _dp, _fp, _ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_int
@@ -167,10 +168,11 @@ def make_config(res, dx, dt, particle_volume, gravity=(0.0, -9.8, 0.0), bound=3,
 
 
 def make_options(checkpoint_every=50, clip_grads=0, clip_value=1e4, sigma_min=1e-4, sort_every=0,
-                 tile_scatter=0) -> mpm_options:
+                 tile_scatter=0, cuda_graphs=1) -> mpm_options:
     o = mpm_options()
     o.checkpoint_every, o.clip_grads, o.clip_value = int(checkpoint_every), int(clip_grads), float(clip_value)
     o.sigma_min, o.sort_every, o.tile_scatter = float(sigma_min), int(sort_every), int(tile_scatter)
+    o.cuda_graphs = int(cuda_graphs)
     return o
 
 
