@@ -104,6 +104,9 @@ typedef struct {
     double v_lin, v_ang;      /* end-effector speeds (m/s, rad/s), > 0 */
     int substeps_per_action;  /* N >= 1 */
     double start_pose[4];     /* tip x, y, z, psi */
+    int unrounded_T;          /* 1: phases 1 and 4 divide their displacements by the real-valued
+                               * step counts (the alternative mapping of Sec. III-B, gradients
+                               * of Appendix A); 0: by the rounded ones (Algorithm 2) */
 } mpm_skill;
 
 typedef struct {
@@ -157,6 +160,52 @@ int mpm_get_state(mpm_handle* h, float* x, float* v, float* C, float* F, int dev
  * checkpoints). A recording forward continues an existing record only if
  * the previous call recorded too. */
 int mpm_forward(mpm_handle* h, int n_substeps, int record);
+
+/* Surface observation and height map (Sec. III-A, "States and
+ * observations"; Eq. (2)). Per instance a res x res square of pixels of
+ * side `size` in the horizontal (x, z) plane (y is up) centred at center;
+ * pixel (i, j) of a point is i = floorf((x - x0) / h), j = floorf((z - z0) /
+ * h) in FP32 with IEEE division, x0 = (float)(center[0] - size/2),
+ * z0 = (float)(center[1] - size/2), h = (float)(size/res); points outside the
+ * square are ignored; pixel index i * res + j. All instances use the same res
+ * (1..4096). The paper's observation is a 40 x 40 square of 0.24 m. */
+typedef struct {
+    double center[2];         /* (x, z) of the square's centre, m */
+    double size;              /* side, m (> 0) */
+    int res;                  /* pixels per side */
+    double tap;               /* height-map splat offset r_p, m (>= 0) */
+} mpm_obs_grid;
+
+/* The observation: per pixel the highest particle of the current state
+ * (largest y; equal heights: the lowest particle index of the instance).
+ * points: n_inst * res^2 * 3 floats, the winners' positions, NaN where a
+ * pixel is empty (may be NULL). counts: n_inst non-empty pixel counts (host,
+ * may be NULL). grids: n_inst entries. */
+int mpm_surface_observation(mpm_handle* h, const mpm_obs_grid* grids, float* points, int* counts, int device_ptrs);
+
+/* The height map: every particle covers the pixels of (x, z), (x +- tap, z)
+ * and (x, z +- tap) (FP32 sums); a pixel starts at 0 and holds the largest y
+ * above 0 of the particles that cover it. maps: n_inst * res^2 floats. */
+int mpm_height_map(mpm_handle* h, const mpm_obs_grid* grids, float* maps, int device_ptrs);
+
+/* The height-map distance of Eq. (2) per instance, loss[i] = sum_pixels
+ * |I - Ihat| (FP64, host), against target_maps (n_inst * res^2 floats), and,
+ * if dL_dx != NULL, its gradient w.r.t. the positions (n_particles * 3,
+ * external order): at each pixel the particle whose height it holds gets
+ * sign(I - Ihat) in y; x and z get 0 (the map is piecewise constant in
+ * them). Equal heights: the lowest particle index holds the pixel. */
+int mpm_loss_hmd(mpm_handle* h, const mpm_obs_grid* grids, const float* target_maps, double* loss, float* dL_dx,
+                 int device_ptrs);
+
+/* The line search of Sec. III-F, batched: instances 0..n_cand-1 of h are the
+ * candidates (the caller has set their start state); each gets mats[k]
+ * and/or skills[k] (either may be NULL), all advance n_substeps in one
+ * forward, and the candidate with the least height-map distance to its
+ * target map wins (ties: the lowest k). losses: n_cand doubles (may be
+ * NULL); *best: the winner. Instances past n_cand advance too. */
+int mpm_line_search(mpm_handle* h, int n_cand, const mpm_material* mats, const mpm_skill* skills, int n_substeps,
+                    const mpm_obs_grid* grids, const float* target_maps, int device_ptrs, double* losses,
+                    int* best);
 
 /* CUDA graphs (option cuda_graphs, on by default). An optimisation loop runs
  * the same rollout again and again: set the state (and material or skill),

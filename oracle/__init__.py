@@ -157,7 +157,7 @@ def _declare(L):
     L.orc_rollout_adjoint.argtypes = ([P, i64] + [_dp] * 4 + [ctypes.c_int, _dp] + [_dp] * 4 + [_dp] * 4
                                       + [_dp, _dp])
     L.orc_rollout_adjoint.restype = ctypes.c_int
-    L.orc_skill_actions.argtypes = [_dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+    L.orc_skill_actions.argtypes = [_dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                     _dp, _ip, _dp]
     L.orc_skill_actions.restype = ctypes.c_int
     L.orc_pose_table.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]
@@ -272,13 +272,16 @@ def rollout_adjoint(p: Params, x0, v0, C0, F0, poses, gx=None, gv=None, gC=None,
                 "material": gmat, "poses": gposes[:nsub]}
 
 
-def skill_actions(theta, v_lin: float, v_ang: float, dt_step: float, max_actions: int = 100000):
-    """Algorithm 2 with rounded phase lengths -> (actions[T,6], T[4], jac[T,6,6])."""
+def skill_actions(theta, v_lin: float, v_ang: float, dt_step: float, max_actions: int = 100000,
+                  unrounded: bool = False):
+    """Algorithm 2 -> (actions[T,6], T[4], jac[T,6,6]); unrounded: phases 1
+    and 4 divide by the real-valued step counts (Sec. III-B alternative)."""
     th = _arr(theta, (6,))
     acts = np.zeros((max_actions, 6))
     jac = np.zeros((max_actions, 6, 6))
     T = (ctypes.c_int * 4)()
-    n = _L().orc_skill_actions(_d(th), v_lin, v_ang, dt_step, max_actions, _d(acts), ctypes.cast(T, _ip), _d(jac))
+    n = _L().orc_skill_actions(_d(th), v_lin, v_ang, dt_step, max_actions, int(bool(unrounded)), _d(acts),
+                               ctypes.cast(T, _ip), _d(jac))
     if n < 0:
         raise ValueError("max_actions too small")
     return acts[:n].copy(), np.array(T[:]), jac[:n].copy()

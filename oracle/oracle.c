@@ -917,7 +917,7 @@ int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const 
 /* (theta_lift = 1 gives the paper's constant 0.01 m).                  */
 /* ------------------------------------------------------------------ */
 int orc_skill_actions(const double theta[6], double v_lin, double v_ang, double dt_step,
-                      int max_actions, double* actions, int T[4], double* jac) {
+                      int max_actions, int unrounded, double* actions, int T[4], double* jac) {
     const double pi = ORC_PI;
     double th_disp = theta[0], th_rot = theta[1], th_ins = theta[2], th_pa = theta[3], th_pd = theta[4],
            th_lift = theta[5];
@@ -939,10 +939,24 @@ int orc_skill_actions(const double theta[6], double v_lin, double v_ang, double 
     int Ttot = T1 + T2 + T3 + T4;
     if (T) { T[0] = T1; T[1] = T2; T[2] = T3; T[3] = T4; }
     if (Ttot > max_actions) return -1;
-    double dx1 = T1 > 0 ? d1 / T1 : 0, drx1 = T1 > 0 ? ph1 / T1 : 0;
+    /* phases 1 and 4 divide by the real-valued step counts in the unrounded
+     * variant (Sec. III-B, the alternative mapping; phases 2 and 3 keep T_2,
+     * T_3); the number of steps stays T_1, T_4 */
+    double Tf4 = Tfp1 >= Tfd4 ? Tfp1 : Tfd4;
+    double div1 = unrounded ? Tf1 : (double)T1, div4 = unrounded ? Tf4 : (double)T4;
+    double dx1 = T1 > 0 ? d1 / div1 : 0, drx1 = T1 > 0 ? ph1 / div1 : 0;
     double dx2 = T2 > 0 ? d2 * cos(ph2) / T2 : 0, dz2 = T2 > 0 ? -d2 * sin(ph2) / T2 : 0;
     double dx3 = T3 > 0 ? d3 * cos(ph3) / T3 : 0, dz3 = T3 > 0 ? d3 * sin(ph3) / T3 : 0;
-    double drx4 = T4 > 0 ? -ph1 / T4 : 0, dz4 = T4 > 0 ? d4 / T4 : 0;
+    double drx4 = T4 > 0 ? -ph1 / div4 : 0, dz4 = T4 > 0 ? d4 / div4 : 0;
+    /* derivatives of the step divisors in the unrounded variant: the active
+     * term of each max (the d term on ties in phase 1, the rotation term on
+     * ties in phase 4, as the paper's case split reads) */
+    const double sd1 = d1 > 0 ? 1.0 : (d1 < 0 ? -1.0 : 0.0), sp1 = ph1 > 0 ? 1.0 : (ph1 < 0 ? -1.0 : 0.0);
+    double dTf1_ddisp = 0, dTf1_drot = 0, dTf4_drot = 0, dTf4_dlift = 0;
+    if (Tfd1 >= Tfp1) dTf1_ddisp = sd1 * 0.12 / (v_lin * dt_step);
+    else dTf1_drot = sp1 * (pi / 3.0) / (v_ang * dt_step);
+    if (Tfp1 >= Tfd4) dTf4_drot = sp1 * (pi / 3.0) / (v_ang * dt_step);
+    else dTf4_dlift = 0.005 / (v_lin * dt_step);
     memset(actions, 0, (size_t)Ttot * 6 * sizeof(double));
     if (jac) memset(jac, 0, (size_t)Ttot * 36 * sizeof(double));
     /* jac index: t*36 + k*6 + j  (k: action component, j: parameter) */
@@ -952,9 +966,15 @@ int orc_skill_actions(const double theta[6], double v_lin, double v_ang, double 
         if (t < T1) {
             a[0] = dx1;
             a[3] = drx1;
-            if (J) {
+            if (J && !unrounded) {
                 J[0 * 6 + 0] = 0.12 / T1;
                 J[3 * 6 + 1] = (pi / 3.0) / T1;
+            } else if (J) {
+                /* d(d1 / Tf1), d(ph1 / Tf1) */
+                J[0 * 6 + 0] = 0.12 / Tf1 - d1 * dTf1_ddisp / (Tf1 * Tf1);
+                J[0 * 6 + 1] = -d1 * dTf1_drot / (Tf1 * Tf1);
+                J[3 * 6 + 0] = -ph1 * dTf1_ddisp / (Tf1 * Tf1);
+                J[3 * 6 + 1] = (pi / 3.0) / Tf1 - ph1 * dTf1_drot / (Tf1 * Tf1);
             }
         } else if (t < T1 + T2) {
             a[0] = dx2;
@@ -977,9 +997,15 @@ int orc_skill_actions(const double theta[6], double v_lin, double v_ang, double 
         } else {
             a[3] = drx4;
             a[1] = dz4;
-            if (J) {
+            if (J && !unrounded) {
                 J[3 * 6 + 1] = -(pi / 3.0) / T4;
                 J[1 * 6 + 5] = 0.005 / T4;
+            } else if (J) {
+                /* d(-ph1 / Tf4), d(d4 / Tf4) */
+                J[3 * 6 + 1] = -(pi / 3.0) / Tf4 + ph1 * dTf4_drot / (Tf4 * Tf4);
+                J[3 * 6 + 5] = ph1 * dTf4_dlift / (Tf4 * Tf4);
+                J[1 * 6 + 1] = -d4 * dTf4_drot / (Tf4 * Tf4);
+                J[1 * 6 + 5] = 0.005 / Tf4 - d4 * dTf4_dlift / (Tf4 * Tf4);
             }
         }
     }

@@ -87,14 +87,17 @@ int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const 
                         double* ax0, double* av0, double* aC0, double* aF0,
                         double gmat[4], double* gposes);
 
-/* Algorithm 2 (skill-to-action mapping) with rounded phase lengths.
+/* Algorithm 2 (skill-to-action mapping), rounded phase lengths by default.
  * theta = (displace, rotate, insert_dist, push_angle, push_dist, lift).
  * dt_step is the global step. Writes up to max_actions actions of 6 doubles
  * in the simulator frame [dx, dy(up), dz, dpsi, 0, 0], the phase lengths
  * T[4], and (if jac != NULL) jac[t*36 + k*6 + j] = d a_t[k] / d theta_j.
+ * unrounded = 1: phases 1 and 4 divide their displacements by the
+ * real-valued step counts T1f, T4f instead of T1, T4 (the alternative
+ * mapping of Sec. III-B, whose gradients Appendix A prints).
  * Returns the number of actions T, or -1 if max_actions is too small. */
 int orc_skill_actions(const double theta[6], double v_lin, double v_ang, double dt_step,
-                      int max_actions, double* actions, int T[4], double* jac);
+                      int max_actions, int unrounded, double* actions, int T[4], double* jac);
 
 /* Per-substep pose table from a start pose (tip[3], psi) and an action list. */
 void orc_pose_table(const double start[4], int n_actions, const double* actions, int substeps_per_action,

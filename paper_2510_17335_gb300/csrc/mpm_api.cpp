@@ -148,6 +148,12 @@ struct mpm_handle {
     DevBuf<unsigned long long> d_fp64;
     DevBuf<int> d_fb_list, d_fb_count;   // particles deferred to the FP64 kernels
     DevBuf<double> d_loss;
+    // surface observation / height map
+    DevBuf<ObsDev> d_obs;
+    DevBuf<unsigned long long> d_keys;
+    DevBuf<float> d_obs_out, d_obs_target;
+    DevBuf<double> d_obs_loss;
+    DevBuf<int> d_obs_count;
 
     // record / backward
     int64_t substep = 0;
@@ -351,14 +357,31 @@ int skill_to_actions(const mpm_skill& s, double dt_step, std::vector<double>& ac
     act.assign((size_t)T * 6, 0.0);
     jac.assign((size_t)T * 36, 0.0);
     const double c2 = std::cos(phi2), s2 = std::sin(phi2), c3 = std::cos(phi3), s3 = std::sin(phi3);
+    // Divisors of phases 1 and 4 and their gradients in (theta_displace,
+    // theta_rotate, theta_lift): the integer step counts, or (unrounded_T)
+    // the real-valued ones, max(|d1| / vl, |phi1| / vw) and max(|phi1| / vw,
+    // d4 / vl), differentiated through their active term (the distance term
+    // of phase 1 and the angle term of phase 4 on ties).
+    double q1 = (double)T1, q4 = (double)T4, gq1[2] = {0.0, 0.0}, gq4[2] = {0.0, 0.0};  // [disp|rot], [rot|lift]
+    if (s.unrounded_T) {
+        const double td1 = std::fabs(d1 / vl), td4 = d4 / vl;
+        const double sd1 = (d1 > 0) - (d1 < 0), sp1 = (phi1 > 0) - (phi1 < 0);
+        if (td1 >= tp1) { q1 = td1; gq1[0] = sd1 * 0.12 / vl; }
+        else { q1 = tp1; gq1[1] = sp1 * (kPi / 3.0) / vw; }
+        if (tp1 >= td4) { q4 = tp1; gq4[0] = sp1 * (kPi / 3.0) / vw; }
+        else { q4 = td4; gq4[1] = 0.005 / vl; }
+    }
     for (long t = 0; t < T; t++) {
         double* a = &act[(size_t)t * 6];
         double* J = &jac[(size_t)t * 36];
         if (t < T1) {
-            a[0] = d1 / T1;
-            a[3] = phi1 / T1;
-            J[0 * 6 + 0] = 0.12 / T1;
-            J[3 * 6 + 1] = (kPi / 3.0) / T1;
+            a[0] = d1 / q1;
+            a[3] = phi1 / q1;
+            // d(d1 / q1), d(phi1 / q1) by the quotient rule
+            J[0 * 6 + 0] = 0.12 / q1 - a[0] * gq1[0] / q1;
+            J[0 * 6 + 1] = -a[0] * gq1[1] / q1;
+            J[3 * 6 + 0] = -a[3] * gq1[0] / q1;
+            J[3 * 6 + 1] = (kPi / 3.0) / q1 - a[3] * gq1[1] / q1;
         } else if (t < T1 + T2) {
             a[0] = d2 * c2 / T2;
             a[1] = -d2 * s2 / T2;
@@ -374,10 +397,12 @@ int skill_to_actions(const mpm_skill& s, double dt_step, std::vector<double>& ac
             J[0 * 6 + 3] = -d3 * s3 * (kPi / 3.0) / T3;
             J[1 * 6 + 3] = d3 * c3 * (kPi / 3.0) / T3;
         } else {
-            a[1] = d4 / T4;
-            a[3] = -phi1 / T4;
-            J[1 * 6 + 5] = 0.005 / T4;
-            J[3 * 6 + 1] = -(kPi / 3.0) / T4;
+            a[1] = d4 / q4;
+            a[3] = -phi1 / q4;
+            J[1 * 6 + 5] = 0.005 / q4 - a[1] * gq4[1] / q4;
+            J[1 * 6 + 1] = -a[1] * gq4[0] / q4;
+            J[3 * 6 + 1] = -(kPi / 3.0) / q4 - a[3] * gq4[0] / q4;
+            J[3 * 6 + 5] = -a[3] * gq4[1] / q4;
         }
     }
     return MPM_OK;
@@ -731,6 +756,8 @@ void mpm_destroy(mpm_handle* h) {
     h->d_state.release(); h->d_x0.release(); h->d_stage.release(); h->d_poses.release(); h->d_target.release();
     h->d_acc.release(); h->d_vout.release(); h->d_flags.release(); h->d_status.release(); h->d_fp64.release();
     h->d_loss.release(); h->d_fb_list.release(); h->d_fb_count.release();
+    h->d_obs.release(); h->d_keys.release(); h->d_obs_out.release(); h->d_obs_target.release();
+    h->d_obs_loss.release(); h->d_obs_count.release();
     for (auto& c : h->ckpt) c.release();
     for (auto& b : h->seg_state) b.release();
     for (auto& b : h->seg_acc) b.release();
@@ -1449,6 +1476,139 @@ int mpm_get_info(mpm_handle* h, mpm_info_t* out) {
     out->kernel_launches = h->launches;
     out->fp64_fallbacks = (int64_t)fb;
     out->graph_launches = h->graph_launches;
+    return MPM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// surface observation, height map, HMD and the line search (Sec. III-A,
+// Eq. (2), Sec. III-F)
+// ---------------------------------------------------------------------------
+static int obs_keys(mpm_handle* h, const mpm_obs_grid* grids, int taps, int* npix_out) {
+    if (!grids) return MPM_ERR_INVALID_ARG;
+    const int n_inst = (int)h->inst.size();
+    const int res = grids[0].res;
+    std::vector<ObsDev> od(n_inst);
+    for (int i = 0; i < n_inst; i++) {
+        const mpm_obs_grid& g = grids[i];
+        if (g.res != res || res < 1 || res > 4096 || !std::isfinite(g.center[0]) || !std::isfinite(g.center[1]) ||
+            !(g.size > 0.0) || !std::isfinite(g.size) || !(g.tap >= 0.0) || !std::isfinite(g.tap))
+            return MPM_ERR_INVALID_ARG;
+        od[i].x0 = (float)(g.center[0] - 0.5 * g.size);
+        od[i].z0 = (float)(g.center[1] - 0.5 * g.size);
+        od[i].h = (float)(g.size / res);
+        od[i].tap = (float)g.tap;
+        od[i].res = res;
+    }
+    const int npix = res * res;
+    RK(set_device(h));
+    RK(h->d_obs.ensure((size_t)n_inst, h->device_bytes));
+    RK(h->d_keys.ensure((size_t)n_inst * npix, h->device_bytes));
+    cudaStream_t s = h->stream;
+    CK(cudaMemcpyAsync(h->d_obs.p, od.data(), od.size() * sizeof(ObsDev), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(h->d_keys.p, 0, (size_t)n_inst * npix * sizeof(unsigned long long), s));
+    CK(launch_obs_keys(h->d_inst.p, h->d_chunk_inst.p, h->n_chunks, h->ncap, h->d_ext_of_slot.p, h->d_state.p,
+                       h->d_obs.p, npix, taps, h->d_keys.p, s));
+    h->launches++;
+    *npix_out = npix;
+    return MPM_OK;
+}
+
+int mpm_surface_observation(mpm_handle* h, const mpm_obs_grid* grids, float* points, int* counts, int device_ptrs) {
+    if (!h || (!points && !counts)) return MPM_ERR_INVALID_ARG;
+    int npix = 0;
+    RK(obs_keys(h, grids, 0, &npix));
+    const int n_inst = (int)h->inst.size();
+    const size_t nf = (size_t)n_inst * npix * 3;
+    cudaStream_t s = h->stream;
+    float* out = points;
+    if (points && !device_ptrs) {
+        RK(h->d_obs_out.ensure(nf, h->device_bytes));
+        out = h->d_obs_out.p;
+    }
+    if (out) {
+        CK(cudaMemsetAsync(out, 0xff, nf * sizeof(float), s));   // all-ones bits: NaN for empty pixels
+        CK(launch_obs_points(h->d_inst.p, h->d_chunk_inst.p, h->n_chunks, h->ncap, h->d_ext_of_slot.p,
+                             h->d_state.p, h->d_obs.p, npix, h->d_keys.p, out, s));
+        h->launches++;
+    }
+    if (counts) {
+        RK(h->d_obs_count.ensure((size_t)n_inst, h->device_bytes));
+        CK(launch_obs_maps(h->d_inst.p, n_inst, npix, h->d_keys.p, nullptr, nullptr, nullptr, nullptr,
+                           h->d_obs_count.p, s));
+        h->launches++;
+        CK(cudaMemcpyAsync(counts, h->d_obs_count.p, (size_t)n_inst * sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    if (points && !device_ptrs) CK(cudaMemcpyAsync(points, out, nf * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MPM_OK;
+}
+
+int mpm_height_map(mpm_handle* h, const mpm_obs_grid* grids, float* maps, int device_ptrs) {
+    if (!h || !maps) return MPM_ERR_INVALID_ARG;
+    int npix = 0;
+    RK(obs_keys(h, grids, 1, &npix));
+    const int n_inst = (int)h->inst.size();
+    const size_t nf = (size_t)n_inst * npix;
+    cudaStream_t s = h->stream;
+    float* out = maps;
+    if (!device_ptrs) {
+        RK(h->d_obs_out.ensure(nf, h->device_bytes));
+        out = h->d_obs_out.p;
+    }
+    CK(launch_obs_maps(h->d_inst.p, n_inst, npix, h->d_keys.p, out, nullptr, nullptr, nullptr, nullptr, s));
+    h->launches++;
+    if (!device_ptrs) CK(cudaMemcpyAsync(maps, out, nf * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MPM_OK;
+}
+
+int mpm_loss_hmd(mpm_handle* h, const mpm_obs_grid* grids, const float* target_maps, double* loss, float* dL_dx,
+                 int device_ptrs) {
+    if (!h || !target_maps || !loss) return MPM_ERR_INVALID_ARG;
+    int npix = 0;
+    RK(obs_keys(h, grids, 1, &npix));
+    const int n_inst = (int)h->inst.size();
+    const size_t nf = (size_t)n_inst * npix, n = (size_t)h->n_ext;
+    cudaStream_t s = h->stream;
+    const float* tgt = target_maps;
+    float* g = dL_dx;
+    if (!device_ptrs) {
+        RK(h->d_obs_target.ensure(nf, h->device_bytes));
+        CK(cudaMemcpyAsync(h->d_obs_target.p, target_maps, nf * sizeof(float), cudaMemcpyHostToDevice, s));
+        tgt = h->d_obs_target.p;
+        if (dL_dx) {
+            RK(h->d_obs_out.ensure(std::max<size_t>(n * 3, 1), h->device_bytes));
+            g = h->d_obs_out.p;
+        }
+    }
+    if (g && n) CK(cudaMemsetAsync(g, 0, n * 3 * sizeof(float), s));
+    RK(h->d_obs_loss.ensure((size_t)n_inst, h->device_bytes));
+    CK(launch_obs_maps(h->d_inst.p, n_inst, npix, h->d_keys.p, nullptr, tgt, h->d_obs_loss.p, g, nullptr, s));
+    h->launches++;
+    CK(cudaMemcpyAsync(loss, h->d_obs_loss.p, (size_t)n_inst * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (dL_dx && !device_ptrs && n) CK(cudaMemcpyAsync(dL_dx, g, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MPM_OK;
+}
+
+int mpm_line_search(mpm_handle* h, int n_cand, const mpm_material* mats, const mpm_skill* skills, int n_substeps,
+                    const mpm_obs_grid* grids, const float* target_maps, int device_ptrs, double* losses,
+                    int* best) {
+    if (!h || n_cand < 1 || n_cand > (int)h->inst.size() || n_substeps < 0 || !grids || !target_maps || !best)
+        return MPM_ERR_INVALID_ARG;
+    for (int k = 0; k < n_cand; k++) {
+        if (mats) RK(mpm_set_material(h, k, &mats[k]));
+        if (skills) RK(mpm_set_shovel_trajectory(h, k, &skills[k]));
+    }
+    RK(mpm_forward(h, n_substeps, 0));
+    std::vector<double> L(h->inst.size());
+    RK(mpm_loss_hmd(h, grids, target_maps, L.data(), nullptr, device_ptrs));
+    int b = 0;
+    for (int k = 1; k < n_cand; k++)
+        if (L[k] < L[b]) b = k;
+    *best = b;
+    if (losses)
+        for (int k = 0; k < n_cand; k++) losses[k] = L[k];
     return MPM_OK;
 }
 

@@ -35,5 +35,18 @@ cudaError_t launch_loss_mse(const InstDev* inst, const int* chunk_inst, int n_ch
                             const int* ext_of_slot, const float* s, const float* target, float* dldx, double* loss,
                             cudaStream_t st);
 
+// surface observation / height map (Sec. III-A): per-pixel winner keys of all
+// instances (keys zeroed by the caller; taps 0: own pixel, 1: 5-tap cross)
+cudaError_t launch_obs_keys(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap,
+                            const int* ext_of_slot, const float* s, const ObsDev* obs, int npix, int taps,
+                            unsigned long long* keys, cudaStream_t st);
+// positions of the winners (points prefilled by the caller)
+cudaError_t launch_obs_points(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap,
+                              const int* ext_of_slot, const float* s, const ObsDev* obs, int npix,
+                              const unsigned long long* keys, float* points, cudaStream_t st);
+// heights, distance to a target map and its gradient, non-empty pixel counts
+// (each output may be null)
+cudaError_t launch_obs_maps(const InstDev* inst, int n_inst, int npix, const unsigned long long* keys, float* maps,
+                            const float* target, double* loss, float* dL_dx, int* counts, cudaStream_t st);
 
 }  // namespace mpm

@@ -1,0 +1,155 @@
+// Surface observation, height map and height-map distance (DDBot, arXiv
+// 2510.17335, Sec. III-A "States and observations", Eq. (2)), for sm_103a.
+//
+// A pixel's winner is found with one 64-bit atomicMax per particle and
+// pixel on the key (ordered FP32 height << 32) | (~local particle index):
+// the highest particle wins, equal heights go to the lowest index, in any
+// launch order. Pixel indices are computed in FP32 with IEEE division,
+// floorf((x - x0) / h), so that they match a CPU evaluation bit for bit.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mpm_launch.h"
+#include "mpm_types.h"
+
+namespace mpm {
+namespace {
+
+__device__ __forceinline__ int obs_pixel(const ObsDev& g, float x, float z) {
+    const float fi = floorf(__fdiv_rn(x - g.x0, g.h)), fj = floorf(__fdiv_rn(z - g.z0, g.h));
+    if (!(fi >= 0.0f && fi < (float)g.res && fj >= 0.0f && fj < (float)g.res)) return -1;
+    return (int)fi * g.res + (int)fj;
+}
+
+// monotone map of a float to an unsigned int (total order of the reals)
+__device__ __forceinline__ unsigned ordered(float y) {
+    const unsigned u = __float_as_uint(y);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float unordered(unsigned o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+__device__ __forceinline__ unsigned long long obs_key(float y, unsigned local) {
+    return ((unsigned long long)ordered(y) << 32) | (unsigned long long)(0xffffffffu - local);
+}
+
+// keys of every instance's pixels; taps = 0: the particle's own pixel
+// (observation), 1: the 5-tap cross and heights above 0 (height map)
+__global__ void __launch_bounds__(kChunk) k_obs_keys(const InstDev* inst, const int* chunk_inst, long long ncap,
+                                                     const int* ext_of_slot, const float* s, const ObsDev* obs,
+                                                     int npix, int taps, unsigned long long* keys) {
+    const int i = chunk_inst[blockIdx.x];
+    const InstDev& I = inst[i];
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (p - I.pbeg >= I.n) return;
+    const float x = s[(kX + 0) * ncap + p], y = s[(kX + 1) * ncap + p], z = s[(kX + 2) * ncap + p];
+    const unsigned local = (unsigned)((long long)ext_of_slot[p] - I.ext_off);
+    const ObsDev g = obs[i];
+    unsigned long long* kk = keys + (long long)i * npix;
+    const unsigned long long key = obs_key(y, local);
+    if (!taps) {
+        const int q = obs_pixel(g, x, z);
+        if (q >= 0) atomicMax(kk + q, key);
+        return;
+    }
+    if (!(y > 0.0f)) return;   // the map starts at 0 and takes only higher values
+    const float tx[5] = {x, x + g.tap, x - g.tap, x, x};
+    const float tz[5] = {z, z, z, z + g.tap, z - g.tap};
+#pragma unroll
+    for (int t = 0; t < 5; t++) {
+        const int q = obs_pixel(g, tx[t], tz[t]);
+        if (q >= 0) atomicMax(kk + q, key);
+    }
+}
+
+// observation points: each winner writes its position into its pixel
+__global__ void __launch_bounds__(kChunk) k_obs_points(const InstDev* inst, const int* chunk_inst, long long ncap,
+                                                       const int* ext_of_slot, const float* s, const ObsDev* obs,
+                                                       int npix, const unsigned long long* keys, float* points) {
+    const int i = chunk_inst[blockIdx.x];
+    const InstDev& I = inst[i];
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (p - I.pbeg >= I.n) return;
+    const float x = s[(kX + 0) * ncap + p], y = s[(kX + 1) * ncap + p], z = s[(kX + 2) * ncap + p];
+    const unsigned local = (unsigned)((long long)ext_of_slot[p] - I.ext_off);
+    const int q = obs_pixel(obs[i], x, z);
+    if (q < 0) return;
+    const long long at = (long long)i * npix + q;
+    if (keys[at] == obs_key(y, local)) {
+        points[3 * at + 0] = x;
+        points[3 * at + 1] = y;
+        points[3 * at + 2] = z;
+    }
+}
+
+// one CTA per instance: pixel heights (0 where empty), optional distance to a
+// target map (FP64, fixed order: deterministic) and the gradient +-1 at each
+// pixel's winner (dL_dx in external order, zeroed by the caller)
+__global__ void __launch_bounds__(256) k_obs_maps(const InstDev* inst, int npix, const unsigned long long* keys,
+                                                  float* maps, const float* target, double* loss, float* dL_dx,
+                                                  int* counts) {
+    const int i = blockIdx.x;
+    const unsigned long long* kk = keys + (long long)i * npix;
+    double acc = 0.0;
+    int cnt = 0;
+    for (int q = threadIdx.x; q < npix; q += blockDim.x) {
+        const unsigned long long k = kk[q];
+        const bool hit = k != 0ull;
+        const float hgt = hit ? unordered((unsigned)(k >> 32)) : 0.0f;
+        cnt += hit;
+        if (maps) maps[(long long)i * npix + q] = hgt;
+        if (target) {
+            const double d = (double)hgt - (double)target[(long long)i * npix + q];
+            acc += fabs(d);
+            if (dL_dx && hit && d != 0.0) {
+                const long long e = inst[i].ext_off + (long long)(0xffffffffu - (unsigned)(k & 0xffffffffull));
+                atomicAdd(dL_dx + 3 * e + 1, d > 0.0 ? 1.0f : -1.0f);
+            }
+        }
+    }
+    __shared__ double sacc[256];
+    __shared__ int scnt[256];
+    sacc[threadIdx.x] = acc;
+    scnt[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sacc[threadIdx.x] += sacc[threadIdx.x + o];
+            scnt[threadIdx.x] += scnt[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (loss) loss[i] = sacc[0];
+        if (counts) counts[i] = scnt[0];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_obs_keys(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap,
+                            const int* ext_of_slot, const float* s, const ObsDev* obs, int npix, int taps,
+                            unsigned long long* keys, cudaStream_t st) {
+    if (n_chunks <= 0) return cudaSuccess;
+    k_obs_keys<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, ncap, ext_of_slot, s, obs, npix, taps, keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_obs_points(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap,
+                              const int* ext_of_slot, const float* s, const ObsDev* obs, int npix,
+                              const unsigned long long* keys, float* points, cudaStream_t st) {
+    if (n_chunks <= 0) return cudaSuccess;
+    k_obs_points<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, ncap, ext_of_slot, s, obs, npix, keys, points);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_obs_maps(const InstDev* inst, int n_inst, int npix, const unsigned long long* keys, float* maps,
+                            const float* target, double* loss, float* dL_dx, int* counts, cudaStream_t st) {
+    if (n_inst <= 0) return cudaSuccess;
+    k_obs_maps<<<n_inst, 256, 0, st>>>(inst, npix, keys, maps, target, loss, dL_dx, counts);
+    return cudaGetLastError();
+}
+
+}  // namespace mpm

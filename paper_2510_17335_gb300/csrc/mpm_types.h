@@ -37,6 +37,13 @@ struct InstDev {
     const float* poses;     // n_poses * 8: tip xyz, psi, tip velocity, psi rate
 };
 
+// Observation / height-map square of one instance (Sec. III-A), FP32 as the
+// pixel index is computed: x0 = cx - size/2, z0 = cz - size/2, h = size/res.
+struct ObsDev {
+    float x0, z0, h, tap;
+    int res;
+};
+
 // Arguments of one substep's kernels (passed by value).
 struct StepArgs {
     const InstDev* inst;

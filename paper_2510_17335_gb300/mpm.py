@@ -54,13 +54,29 @@ class mpm_options(ctypes.Structure):
 
 class mpm_skill(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double * 6), ("v_lin", ctypes.c_double), ("v_ang", ctypes.c_double),
-                ("substeps_per_action", ctypes.c_int), ("start_pose", ctypes.c_double * 4)]
+                ("substeps_per_action", ctypes.c_int), ("start_pose", ctypes.c_double * 4),
+                ("unrounded_T", ctypes.c_int)]
 
 
 class mpm_info_t(ctypes.Structure):
     _fields_ = [("n_inst", ctypes.c_int), ("n_particles", ctypes.c_int64), ("substep", ctypes.c_int64),
                 ("recorded", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("fp64_fallbacks", ctypes.c_int64), ("graph_launches", ctypes.c_int64)]
+
+
+class mpm_obs_grid(ctypes.Structure):
+    _fields_ = [("center", ctypes.c_double * 2), ("size", ctypes.c_double), ("res", ctypes.c_int),
+                ("tap", ctypes.c_double)]
+
+
+def make_obs_grid(center_xz, size: float = 0.24, res: int = 40, tap: float = 0.0) -> mpm_obs_grid:
+    """Observation / height-map square (Sec. III-A): res x res pixels of side
+    size in the (x, z) plane centred at center_xz; tap is the height-map
+    splat offset."""
+    g = mpm_obs_grid()
+    g.center[0], g.center[1] = float(center_xz[0]), float(center_xz[1])
+    g.size, g.res, g.tap = float(size), int(res), float(tap)
+    return g
 
 
 _vp, _dp, _fp, _ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_int
@@ -91,6 +107,11 @@ EXPORTS = {
     "mpm_profile_read": (_ip, [_vp, _ip, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "mpm_kernel_name": (ctypes.c_char_p, [_ip]),
     "mpm_loss_mse_noalloc": (_ip, [_fp, _fp, ctypes.c_int64, _fp, _dp, _vp]),
+    "mpm_surface_observation": (_ip, [_vp, ctypes.POINTER(mpm_obs_grid), _fp, ctypes.POINTER(ctypes.c_int), _ip]),
+    "mpm_height_map": (_ip, [_vp, ctypes.POINTER(mpm_obs_grid), _fp, _ip]),
+    "mpm_loss_hmd": (_ip, [_vp, ctypes.POINTER(mpm_obs_grid), _fp, _dp, _fp, _ip]),
+    "mpm_line_search": (_ip, [_vp, _ip, ctypes.POINTER(mpm_material), ctypes.POINTER(mpm_skill), _ip,
+                              ctypes.POINTER(mpm_obs_grid), _fp, _ip, _dp, ctypes.POINTER(ctypes.c_int)]),
     "mpm_destroy": (None, [_vp]),
     "mpm_error_string": (ctypes.c_char_p, [_ip]),
     "mpm_version": (_ip, []),
@@ -167,6 +188,17 @@ def make_config(res, dx, dt, particle_volume, gravity=(0.0, -9.8, 0.0), bound=3,
     return c
 
 
+def make_skill(theta, v_lin, v_ang, substeps_per_action, start_pose, unrounded_T=False) -> mpm_skill:
+    """Skill parameters (Sec. III-B, Algorithm 2); unrounded_T selects the
+    alternative mapping that divides phases 1 and 4 by real-valued step counts."""
+    s = mpm_skill()
+    s.theta[:] = [float(t) for t in theta]
+    s.v_lin, s.v_ang, s.substeps_per_action = float(v_lin), float(v_ang), int(substeps_per_action)
+    s.start_pose[:] = [float(p) for p in start_pose]
+    s.unrounded_T = int(bool(unrounded_T))
+    return s
+
+
 def make_options(checkpoint_every=50, clip_grads=0, clip_value=1e4, sigma_min=1e-4, sort_every=0,
                  tile_scatter=0, cuda_graphs=1) -> mpm_options:
     o = mpm_options()
@@ -230,11 +262,8 @@ class Simulation:
                                            int(substeps_per_action)), "mpm_set_shovel_actions")
         self.n_actions[inst] = a.shape[0]
 
-    def set_skill(self, inst: int, theta, v_lin, v_ang, substeps_per_action, start_pose):
-        s = mpm_skill()
-        s.theta[:] = [float(t) for t in theta]
-        s.v_lin, s.v_ang, s.substeps_per_action = float(v_lin), float(v_ang), int(substeps_per_action)
-        s.start_pose[:] = [float(p) for p in start_pose]
+    def set_skill(self, inst: int, theta, v_lin, v_ang, substeps_per_action, start_pose, unrounded_T=False):
+        s = make_skill(theta, v_lin, v_ang, substeps_per_action, start_pose, unrounded_T)
         check(lib().mpm_set_shovel_trajectory(self.h, inst, ctypes.byref(s)), "mpm_set_shovel_trajectory")
         self.n_actions[inst] = lib().mpm_num_actions(self.h, inst)
 
@@ -330,6 +359,55 @@ class Simulation:
         check(lib().mpm_grid_mass(self.h, out.ctypes.data_as(_dp)), "mpm_grid_mass")
         return out
 
+    def _grids(self, grids):
+        if isinstance(grids, mpm_obs_grid):
+            grids = [grids] * self.n_inst
+        assert len(grids) == self.n_inst
+        return (mpm_obs_grid * self.n_inst)(*grids)
+
+    def surface_observation(self, grids):
+        """(points [n_inst, res*res, 3] with NaN for empty pixels, counts [n_inst])."""
+        ga = self._grids(grids)
+        npix = ga[0].res * ga[0].res
+        pts = np.empty((self.n_inst, npix, 3), np.float32)
+        cnt = (ctypes.c_int * self.n_inst)()
+        check(lib().mpm_surface_observation(self.h, ga, pts.ctypes.data_as(ctypes.c_void_p), cnt, 0),
+              "mpm_surface_observation")
+        return pts, np.array(cnt[:], np.int64)
+
+    def height_map(self, grids) -> np.ndarray:
+        """[n_inst, res, res] height maps."""
+        ga = self._grids(grids)
+        res = ga[0].res
+        out = np.empty((self.n_inst, res, res), np.float32)
+        check(lib().mpm_height_map(self.h, ga, out.ctypes.data_as(ctypes.c_void_p), 0), "mpm_height_map")
+        return out
+
+    def loss_hmd(self, grids, target_maps, want_grad: bool = True):
+        """(loss [n_inst] (FP64), dL/dx [n, 3] or None)."""
+        ga = self._grids(grids)
+        tm = np.ascontiguousarray(target_maps, np.float32)
+        assert tm.size == self.n_inst * ga[0].res * ga[0].res
+        L = np.zeros(self.n_inst, np.float64)
+        g = np.empty((self.n, 3), np.float32) if want_grad else None
+        check(lib().mpm_loss_hmd(self.h, ga, tm.ctypes.data_as(ctypes.c_void_p), L.ctypes.data_as(_dp),
+                                 g.ctypes.data_as(ctypes.c_void_p) if g is not None else None, 0), "mpm_loss_hmd")
+        return L, g
+
+    def line_search(self, n_substeps: int, grids, target_maps, materials=None, skills=None):
+        """Batched line search (Sec. III-F): candidate k runs as instance k
+        with materials[k] / skills[k]; returns (best k, losses)."""
+        n_cand = len(materials) if materials is not None else len(skills)
+        ga = self._grids(grids)
+        tm = np.ascontiguousarray(target_maps, np.float32)
+        mats = (mpm_material * n_cand)(*[mpm_material(*map(float, m)) for m in materials]) if materials else None
+        sk = (mpm_skill * n_cand)(*skills) if skills else None
+        L = np.zeros(n_cand, np.float64)
+        best = ctypes.c_int()
+        check(lib().mpm_line_search(self.h, n_cand, mats, sk, int(n_substeps), ga, tm.ctypes.data_as(ctypes.c_void_p),
+                                    0, L.ctypes.data_as(_dp), ctypes.byref(best)), "mpm_line_search")
+        return int(best.value), L
+
     def info(self) -> dict:
         i = mpm_info_t()
         check(lib().mpm_get_info(self.h, ctypes.byref(i)), "mpm_get_info")
@@ -351,7 +429,8 @@ def simulation_from_workloads(workloads, options: Optional[mpm_options] = None, 
     for i, w in enumerate(workloads):
         t = w.traj
         if t.theta is not None:
-            sim.set_skill(i, t.theta, t.v_lin, t.v_ang, t.substeps_per_action, t.start_pose)
+            sim.set_skill(i, t.theta, t.v_lin, t.v_ang, t.substeps_per_action, t.start_pose,
+                          unrounded_T=getattr(t, "unrounded", False))
         elif t.actions is not None:
             sim.set_actions(i, t.start_pose, t.actions, t.substeps_per_action)
     return sim

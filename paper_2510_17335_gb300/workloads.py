@@ -32,6 +32,7 @@ class Trajectory:
     v_lin: float = 0.0
     v_ang: float = 0.0
     actions: Optional[np.ndarray] = None     # scripted: [T, 6] in the simulator frame
+    unrounded: bool = False                  # skill: phases 1 and 4 by real-valued step counts
 
 
 @dataclass

@@ -15,7 +15,8 @@ def oracle_params(w, particle_collision=1, shovel_on=1, clip=0, gravity=None):
 def oracle_actions(w):
     t = w.traj
     if t.theta is not None:
-        acts, T, jac = oracle.skill_actions(t.theta, t.v_lin, t.v_ang, t.substeps_per_action * w.dt)
+        acts, T, jac = oracle.skill_actions(t.theta, t.v_lin, t.v_ang, t.substeps_per_action * w.dt,
+                                            unrounded=t.unrounded)
         return acts, jac
     return np.asarray(t.actions, np.float64), None
 

@@ -109,15 +109,17 @@ def test_adjoint_matches_oracle_contact_scenario():
     assert e.max() < BAR
 
 
-def test_adjoint_skill_theta_gradient():
-    """dL/dtheta through Algorithm 2's Jacobian (rounded T, frozen): the
-    library's chain against the oracle's (pose-table adjoint, then the
-    Jacobian), on a bed dug by the skill."""
+@pytest.mark.parametrize("unrounded", [False, True])
+def test_adjoint_skill_theta_gradient(unrounded):
+    """dL/dtheta through Algorithm 2's Jacobian (frozen T; rounded or, for
+    the alternative mapping of Sec. III-B, real-valued phase-1/4 step
+    counts): the library's chain against the oracle's (pose-table adjoint,
+    then the Jacobian), on a bed dug by the skill."""
     res, dx = 32, 1.0 / 32
     x0 = W.lattice_bed(31, (10, 5, 8), (11 * dx, 3 * dx, 12 * dx), dx)
     top = 8 * dx
     traj = W.Trajectory((13.5 * dx, top - 0.005, 16 * dx, 0.0), 4, theta=(0.4, 0.3, 0.55, 0.2, -0.2, 0.5),
-                        v_lin=25.0, v_ang=250.0)
+                        v_lin=25.0, v_ang=250.0, unrounded=unrounded)
     w = W.Workload("skill", (res,) * 3, dx, 1e-4, 40, 1e5, 0.3, 1500.0, 30.0, dx ** 3 / 8, x0, traj,
                    shovel_half=(0.02, 0.06, 0.1))
     seed = _seed(w, 3)

@@ -127,3 +127,98 @@ def test_demo_theta_constants():
     g = GOLDEN["demo_skill"]
     assert W.DEMO_THETA[1:5] == (g["theta_rotate"], g["theta_insert_dist"], g["theta_push_angle"],
                                  g["theta_push_dist"])
+
+
+# ---------------------------------------------------------------------------
+# unrounded phase-1/4 step counts (Sec. III-B alternative; Appendix A)
+# ---------------------------------------------------------------------------
+V_L, V_W, DT = 2.5, 25.0, 1e-3
+
+
+def _phase_sum(jac, T, phase, j):
+    t0 = int(sum(T[:phase]))
+    return jac[t0:t0 + T[phase]].sum(axis=(0, 1))[j]
+
+
+def _cases(theta):
+    d1 = theta[0] * 0.12
+    ph1 = theta[1] * np.pi / 3
+    d4 = (theta[5] + 1) * 0.005
+    Tfd1, Tfp1 = abs(d1 / (V_L * DT)), abs(ph1 / (V_W * DT))
+    Tfd4 = d4 / (V_L * DT)
+    return Tfd1, Tfp1, Tfd4, d4
+
+
+@pytest.mark.parametrize("theta", [
+    (0.5, 0.2, 0.8, 0.0, -0.5, 1.0),     # phase 1: d dominates; phase 4: lift dominates
+    (0.1, 0.8, 0.3, 0.2, 0.1, 0.5),      # phase 1: rotation dominates; phase 4: rotation dominates
+    (0.9, 0.45, -0.5, -0.8, 0.9, -0.4),
+])
+def test_unrounded_summed_gradients_match_appendix_a(theta):
+    """Appendix A's closed forms for the unrounded variant (positive
+    theta_displace / theta_rotate branches and the third cases)."""
+    acts, T, jac = oracle.skill_actions(theta, V_L, V_W, DT, unrounded=True)
+    assert (T > 0).all()
+    Tfd1, Tfp1, Tfd4, d4 = _cases(theta)
+    th_d, th_r = theta[0], theta[1]
+    T1, T4 = T[0], T[3]
+    # d a[0:T1] / d theta_displace
+    if Tfd1 >= Tfp1:
+        want = T1 * (-np.pi * th_r * V_L * DT) / (0.36 * th_d ** 2)
+    else:
+        want = T1 * (0.12 * V_W * DT) / (abs(th_r) * np.pi / 3)
+    assert np.isclose(_phase_sum(jac, T, 0, 0), want, rtol=1e-12, atol=1e-15)
+    # d a[0:T1] / d theta_rotate
+    if Tfp1 > Tfd1:
+        want = T1 * (-0.36 * th_d * V_W * DT) / (th_r ** 2 * np.pi)
+    else:
+        want = T1 * (np.pi / 3 * V_L * DT) / (abs(th_d) * 0.12)
+    assert np.isclose(_phase_sum(jac, T, 0, 1), want, rtol=1e-12, atol=1e-15)
+    # d a[T1+T2+T3 : T] / d theta_rotate
+    if Tfp1 >= Tfd4:
+        want = T4 * (-3 * d4 * V_W * DT) / (th_r ** 2 * np.pi)
+    else:
+        want = T4 * (-np.pi * V_L * DT) / (3 * d4)
+    assert np.isclose(_phase_sum(jac, T, 3, 1), want, rtol=1e-12, atol=1e-15)
+    # phase 2 keeps the rounded T2: -d2 pi/3 (sin(ph1 + pi/2) + cos(ph1 + pi/2))
+    d2 = (theta[2] + 1) * 0.03
+    ph1 = th_r * np.pi / 3
+    want = -d2 * np.pi / 3 * (np.sin(ph1 + np.pi / 2) + np.cos(ph1 + np.pi / 2))
+    assert np.isclose(_phase_sum(jac, T, 1, 1), want, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("theta", [
+    (0.5, 0.2, 0.8, 0.0, -0.5, 1.0),
+    (-0.5, 0.2, 0.8, 0.0, -0.5, 1.0),    # theta_displace < 0
+    (0.1, -0.8, 0.3, 0.2, 0.1, 0.5),     # theta_rotate < 0, rotation dominating phases 1 and 4
+    (-0.2, -0.9, -0.3, 0.6, -0.2, -0.7),
+])
+def test_unrounded_jacobian_matches_fd_with_frozen_T(theta):
+    """Every branch against central differences of the mapping itself (for
+    frozen integer step counts)."""
+    acts, T, jac = oracle.skill_actions(theta, V_L, V_W, DT, unrounded=True)
+    h = 1e-7
+    for j in range(6):
+        tp, tm = np.array(theta, float), np.array(theta, float)
+        tp[j] += h
+        tm[j] -= h
+        ap, Tp, _ = oracle.skill_actions(tp, V_L, V_W, DT, unrounded=True)
+        am, Tm, _ = oracle.skill_actions(tm, V_L, V_W, DT, unrounded=True)
+        assert (Tp == T).all() and (Tm == T).all()
+        fd = (ap - am) / (2 * h)
+        assert np.allclose(jac[:, :, j], fd, rtol=1e-6, atol=1e-9), j
+
+
+def test_unrounded_per_step_displacements():
+    """Phases 1 and 4 move by (total / T_float) per step; phases 2 and 3 are
+    those of the rounded mapping."""
+    theta = (0.5, 0.2, 0.8, 0.0, -0.5, 1.0)
+    ar, Tr, _ = oracle.skill_actions(theta, V_L, V_W, DT)
+    au, Tu, _ = oracle.skill_actions(theta, V_L, V_W, DT, unrounded=True)
+    assert (Tr == Tu).all()
+    Tfd1, Tfp1, Tfd4, d4 = _cases(theta)
+    T1, T2, T3, T4 = Tu
+    assert np.allclose(au[:T1, 0], theta[0] * 0.12 / max(Tfd1, Tfp1), rtol=1e-14)
+    assert np.allclose(au[:T1, 3], theta[1] * np.pi / 3 / max(Tfd1, Tfp1), rtol=1e-14)
+    assert np.array_equal(au[T1:T1 + T2 + T3], ar[T1:T1 + T2 + T3])
+    assert np.allclose(au[T1 + T2 + T3:, 1], d4 / max(Tfp1, Tfd4), rtol=1e-14)
