@@ -77,6 +77,9 @@ class _Params(ctypes.Structure):
         ("shovel_on", ctypes.c_int),
         ("clip_grads", ctypes.c_int),
         ("clip_value", ctypes.c_double),
+        ("grad_scale", ctypes.c_int),
+        ("oom_star", ctypes.c_double),
+        ("grad_delta", ctypes.c_double),
     ]
 
 
@@ -100,6 +103,9 @@ class Params:
     shovel_on: int = 1
     clip_grads: int = 0
     clip_value: float = 1e4
+    grad_scale: int = 0          # 1 dynamic scaling, 2 normalisation (Sec. III-E)
+    oom_star: float = 4.0
+    grad_delta: float = 1e-6
 
     def c(self) -> _Params:
         p = _Params()
@@ -113,6 +119,7 @@ class Params:
         p.sigma_min = self.sigma_min
         p.shovel_half[:] = [float(h) for h in self.shovel_half]
         p.shovel_on, p.clip_grads, p.clip_value = self.shovel_on, self.clip_grads, self.clip_value
+        p.grad_scale, p.oom_star, p.grad_delta = self.grad_scale, self.oom_star, self.grad_delta
         return p
 
 
@@ -162,6 +169,7 @@ def _declare(L):
     L.orc_skill_actions.restype = ctypes.c_int
     L.orc_pose_table.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]
     L.orc_pose_table_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
+    L.orc_grad_op.argtypes = [P, _dp, i64]
     G = ctypes.POINTER(_ObsGrid)
     _fp = ctypes.POINTER(ctypes.c_float)
     _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -345,3 +353,11 @@ def hmd(g: ObsGrid, x, Ihat) -> tuple[float, np.ndarray]:
     gc = g.c()
     L = _L().orc_hmd(ctypes.byref(gc), x.shape[0], xp, _d(Ih), _d(grad))
     return float(L), grad
+
+
+def grad_op(p: Params, g) -> np.ndarray:
+    """Sec. III-E regulariser (clip / dynamic scaling / normalisation) of one vector."""
+    g = np.ascontiguousarray(np.asarray(g, np.float64).reshape(-1)).copy()
+    pc = p.c()
+    _L().orc_grad_op(ctypes.byref(pc), _d(g), g.size)
+    return g

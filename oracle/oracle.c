@@ -683,6 +683,31 @@ static double clipv(double g, const orc_params* p) {
     return g;
 }
 
+/* Clipping, dynamic scaling or normalisation of one whole adjoint vector
+ * (Sec. III-E): the key variables are the particles' x, v, F and the grid's
+ * m and velocities before and after the contact, each as one vector. */
+void orc_grad_op(const orc_params* p, double* g, int64_t n) {
+    if (p->clip_grads) {
+        for (int64_t i = 0; i < n; i++) g[i] = clipv(g[i], p);
+        return;
+    }
+    if (p->grad_scale == 1) {
+        double mx = 0.0;
+        for (int64_t i = 0; i < n; i++) mx = fabs(g[i]) > mx ? fabs(g[i]) : mx;
+        if (!(mx > 0.0)) return;
+        const double doom = round(log10(mx)) - p->oom_star;
+        if (doom > 0.0) {
+            const double div = pow(10.0, doom) + p->grad_delta;
+            for (int64_t i = 0; i < n; i++) g[i] /= div;
+        }
+    } else if (p->grad_scale == 2) {
+        double ss = 0.0;
+        for (int64_t i = 0; i < n; i++) ss += g[i] * g[i];
+        const double div = sqrt(ss) + p->grad_delta;
+        for (int64_t i = 0; i < n; i++) g[i] /= div;
+    }
+}
+
 int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const double* v0,
                         const double* C0, const double* F0, int nsub, const double* poses,
                         const double* gx, const double* gv, const double* gC, const double* gF,
@@ -752,9 +777,10 @@ int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const 
             mm(IC, F + 9 * q, Ft);
             orc_constitutive(Ft, mu, lam, alpha, p->sigma_min, Fn, tau + 9 * q, NULL);
         }
-        /* clipping of the particle adjoints (Sec. III-E) */
-        for (int64_t i = 0; i < n * 3; i++) { ax[i] = clipv(ax[i], p); av[i] = clipv(av[i], p); }
-        for (int64_t i = 0; i < n * 9; i++) aF[i] = clipv(aF[i], p);
+        /* regularised particle adjoints (Sec. III-E) */
+        orc_grad_op(p, ax, n * 3);
+        orc_grad_op(p, av, n * 3);
+        orc_grad_op(p, aF, n * 9);
 
         /* reverse of advection, particle collision and G2P; the partial
          * adjoint of x is kept in ax, the grid velocity adjoint goes to avo */
@@ -797,8 +823,10 @@ int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const 
                     }
             for (int k = 0; k < 3; k++) ax[3 * q + k] = gxp[k];
         }
-        /* reverse of the grid update */
-        for (int64_t i = 0; i < 3 * G; i++) avo[i] = clipv(avo[i], p);
+        /* reverse of the grid update: the adjoint of the velocity after the
+         * contact (regularised), then of the velocity before it (for every
+         * node, then regularised), then of the mass (regularised) */
+        orc_grad_op(p, avo, 3 * G);
         memset(am, 0, G * sizeof(double));
         memset(amv, 0, 3 * G * sizeof(double));
         for (int i = 0; i < p->res[0]; i++)
@@ -816,14 +844,19 @@ int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const 
                     double q[3] = {i * p->dx, j * p->dx, k * p->dx}, gq[3] = {0, 0, 0};
                     double gvg[3] = {0, 0, 0};
                     shovel_project_adjoint(p, vg, q, pose, avo + 3 * id, gvg, gq, gpose);
-                    double dot = 0;
-                    for (int a = 0; a < 3; a++) {
-                        gvg[a] = clipv(gvg[a] * mask[a], p);
-                        amv[3 * id + a] = gvg[a] / m[id];
-                        dot += gvg[a] * mv[3 * id + a];
-                    }
-                    am[id] = clipv(-dot / (m[id] * m[id]), p);
+                    for (int a = 0; a < 3; a++) amv[3 * id + a] = gvg[a] * mask[a];   /* v-bar before the contact */
                 }
+        orc_grad_op(p, amv, 3 * G);
+        for (int64_t id = 0; id < G; id++) {
+            if (!(m[id] > 0)) continue;
+            double dot = 0;
+            for (int a = 0; a < 3; a++) {
+                dot += amv[3 * id + a] * mv[3 * id + a];
+                amv[3 * id + a] /= m[id];
+            }
+            am[id] = -dot / (m[id] * m[id]);
+        }
+        orc_grad_op(p, am, G);
         /* reverse of P2G and the constitutive step */
         for (int64_t q = 0; q < n; q++) {
             const double* xp = x + 3 * q;

@@ -36,7 +36,17 @@ typedef struct {
     int shovel_on;             /* 0: no shovel */
     int clip_grads;            /* clip adjoints of key variables (Sec. III-E) */
     double clip_value;
+    int grad_scale;            /* 0 none, 1 dynamic scaling, 2 normalisation of the same
+                                * adjoint vectors (Sec. III-E); not with clip_grads */
+    double oom_star;           /* maximal order of magnitude (dynamic scaling) */
+    double grad_delta;         /* the small constant delta of both operations */
 } orc_params;
+
+/* The gradient regularisers of Sec. III-E on one adjoint vector g[n]:
+ * grad_scale 1: g /= 10^doom + delta with doom = round(log10 max|g_i|) -
+ * oom_star, only when doom > 0; 2: g /= ||g||_2 + delta. clip_grads clips
+ * each entry to [-clip_value, clip_value] instead. */
+void orc_grad_op(const orc_params* p, double* g, int64_t n);
 
 /* 3x3 SVD with proper rotations U, V (det +1) and S sorted by magnitude,
  * S[2] carrying the sign of det(F). */
