@@ -467,7 +467,7 @@ def kernel_counters(name: str):
 def kernel_source_sha() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("mpm_kernels.cu", "mpm_device.cuh", "mpm_types.h"):
+    for f in ("mpm_kernels.cu", "mpm_device.cuh", "mpm_types.h", "mpm_reg.h"):
         h.update(open(os.path.join(ROOT, "paper_2510_17335_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

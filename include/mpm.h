@@ -93,6 +93,14 @@ typedef struct {
     int tile_scatter;         /* [0] sum the 27-node scatters in shared-memory tiles per CTA */
     int cuda_graphs;          /* [1] replay repeated identical mpm_forward / mpm_backward calls
                                * from CUDA graphs (see below) */
+    int grad_scale;           /* [0] regularise the adjoints of the particles' x, v, F and of the
+                               * grid's velocities (after, before the contact) and mass, each as
+                               * one vector per substep and instance (Sec. III-E): 1 dynamic
+                               * scaling, g /= 10^doom + delta, doom = round(log10 max|g|) -
+                               * oom_star when positive; 2 normalisation, g /= ||g|| + delta.
+                               * Not together with clip_grads. */
+    double oom_star;          /* [4] */
+    double grad_delta;        /* [1e-6] */
 } mpm_options;
 
 /* Digging skill (Sec. III-B): theta = (displace, rotate, insert_dist,

@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libmpm_gb300.so")
 SOURCES = ["mpm_kernels.cu", "mpm_api.cpp", "mpm_noalloc.cu", "mpm_obs.cu"]
-HEADERS = ["mpm_device.cuh", "mpm_types.h", "mpm_launch.h"]
+HEADERS = ["mpm_device.cuh", "mpm_types.h", "mpm_launch.h", "mpm_reg.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

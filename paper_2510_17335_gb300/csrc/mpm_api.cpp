@@ -15,6 +15,7 @@
 
 #include "../../include/mpm.h"
 #include "mpm_launch.h"
+#include "mpm_reg.h"
 #include "mpm_types.h"
 
 using namespace mpm;
@@ -173,6 +174,7 @@ struct mpm_handle {
     bool gacc_dirty = true;
     DevBuf<float> d_adj;
     DevBuf<double> d_gmat, d_gpose;
+    DevBuf<double> d_pstat, d_gstat, d_gpose_raw;   // Sec. III-E regulariser statistics
     bool have_grad = false;
     int tile_scatter = 1;
     // particle sort by grid block
@@ -654,7 +656,9 @@ int mpm_create(int n_inst, const mpm_config* cfgs, const mpm_material* mats, con
                 }
     }
     if (opts && (opts->checkpoint_every < 1 || !(opts->clip_value > 0) || !(opts->sigma_min > 0) ||
-                 opts->sort_every < 0))
+                 opts->sort_every < 0 || opts->grad_scale < 0 || opts->grad_scale > 2 ||
+                 (opts->grad_scale && opts->clip_grads) || !std::isfinite(opts->oom_star) ||
+                 !(opts->grad_delta > 0) || !std::isfinite(opts->grad_delta)))
         return MPM_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -671,6 +675,9 @@ int mpm_create(int n_inst, const mpm_config* cfgs, const mpm_material* mats, con
     h->opt.sort_every = 0;
     h->opt.tile_scatter = 0;
     h->opt.cuda_graphs = 1;
+    h->opt.grad_scale = 0;
+    h->opt.oom_star = 4.0;
+    h->opt.grad_delta = 1e-6;
     if (opts) h->opt = *opts;
     h->tile_scatter = h->opt.tile_scatter ? 1 : 0;
     h->n_ext = n_ext;
@@ -766,6 +773,7 @@ void mpm_destroy(mpm_handle* h) {
     for (auto& b : h->seg_spec) b.release();
     h->d_gacc.release();
     h->d_adj.release(); h->d_gmat.release(); h->d_gpose.release();
+    h->d_pstat.release(); h->d_gstat.release(); h->d_gpose_raw.release();
     h->d_state2.release(); h->d_adj2.release(); h->d_ext2.release(); h->d_key.release(); h->d_rank.release();
     h->d_bcount.release(); h->d_bscan.release(); h->d_part.release(); h->d_perm.release(); h->d_ext_rec.release();
     for (auto& b : h->seg_perm) b.release();
@@ -1137,6 +1145,17 @@ static int backward_launch(mpm_handle* h, const float* gx, const float* gv, bool
     h->launches++;
     CK(cudaMemsetAsync(h->d_gmat.p, 0, (size_t)n_inst * 4 * sizeof(double), s));
     CK(cudaMemsetAsync(h->d_gpose.p, 0, (size_t)h->rec_len * n_inst * 8 * sizeof(double), s));
+    const int gscale = h->opt.grad_scale;
+    if (gscale) {
+        // statistics of every state's particle adjoints and every substep's
+        // grid adjoints (Sec. III-E); the seed's first
+        CK(cudaMemsetAsync(h->d_pstat.p, 0, (size_t)(h->rec_len + 1) * n_inst * 3 * sizeof(double), s));
+        CK(cudaMemsetAsync(h->d_gstat.p, 0, (size_t)h->rec_len * n_inst * 3 * sizeof(double), s));
+        CK(cudaMemsetAsync(h->d_gpose_raw.p, 0, (size_t)h->rec_len * n_inst * 8 * sizeof(double), s));
+        CK(launch_adj_stats(h->d_inst.p, h->d_chunk_inst.p, h->n_chunks, h->ncap, h->d_adj.p, gscale,
+                            h->d_pstat.p + (size_t)h->rec_len * n_inst * 3, s));
+        h->launches++;
+    }
     const int64_t n_seg = (h->rec_len + K - 1) / K;
     for (int64_t j = n_seg - 1; j >= 0; j--) {
         const int64_t seg_begin = j * K;
@@ -1159,6 +1178,16 @@ static int backward_launch(mpm_handle* h, const float* gx, const float* gv, bool
             A.gacc = h->d_gacc.p;
             A.gmat = h->d_gmat.p;
             A.gpose = h->d_gpose.p + (size_t)(seg_begin + i) * n_inst * 8;
+            if (gscale) {
+                const size_t r = (size_t)(seg_begin + i);
+                A.gscale = gscale;
+                A.oom = (float)h->opt.oom_star;
+                A.gdelta = (float)h->opt.grad_delta;
+                A.pstat_in = h->d_pstat.p + (r + 1) * n_inst * 3;
+                A.pstat_out = h->d_pstat.p + r * n_inst * 3;
+                A.gstat = h->d_gstat.p + r * n_inst * 3;
+                A.gpose_raw = h->d_gpose_raw.p + r * n_inst * 8;
+            }
             RK(run_adjoint_substep(h, A));
             h->seg_dirty[i] = 0;
         }
@@ -1225,6 +1254,11 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, int devi
     RK(h->d_adj.ensure(state_floats, h->device_bytes));
     RK(h->d_gmat.ensure((size_t)n_inst * 4, h->device_bytes));
     RK(h->d_gpose.ensure((size_t)h->rec_len * n_inst * 8, h->device_bytes));
+    if (h->opt.grad_scale) {
+        RK(h->d_pstat.ensure((size_t)(h->rec_len + 1) * n_inst * 3, h->device_bytes));
+        RK(h->d_gstat.ensure((size_t)h->rec_len * n_inst * 3, h->device_bytes));
+        RK(h->d_gpose_raw.ensure((size_t)h->rec_len * n_inst * 8, h->device_bytes));
+    }
     cudaStream_t s = h->stream;
     // seed the adjoint of the final state from library-owned copies, so
     // that a replayed graph never holds a caller's pointer
@@ -1241,7 +1275,22 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, int devi
     std::vector<double> gm((size_t)n_inst * 4), gp((size_t)h->rec_len * n_inst * 8);
     CK(cudaMemcpyAsync(gm.data(), h->d_gmat.p, gm.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(gp.data(), h->d_gpose.p, gp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    std::vector<double> gst, gpr;
+    if (h->opt.grad_scale) {
+        gst.resize((size_t)h->rec_len * n_inst * 3);
+        gpr.resize(gp.size());
+        CK(cudaMemcpyAsync(gst.data(), h->d_gstat.p, gst.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(gpr.data(), h->d_gpose_raw.p, gpr.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaStreamSynchronize(s));
+    if (h->opt.grad_scale) {
+        // the grid kernel's pose adjoint is linear in the post-contact
+        // velocity adjoint: scale it by that vector's factor
+        for (size_t r = 0; r < (size_t)h->rec_len * n_inst; r++) {
+            const double s0 = reg_factor(h->opt.grad_scale, gst[3 * r], h->opt.oom_star, h->opt.grad_delta);
+            for (int k = 0; k < 8; k++) gp[8 * r + k] += s0 * gpr[8 * r + k];
+        }
+    }
     const int st = read_status(h);
     // material chain: mu(E, nu), lambda(E, nu), alpha(phi), m_p = rho V_p
     for (int i = 0; i < n_inst; i++) {

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "mpm_types.h"
+#include "mpm_reg.h"
 
 #if defined(__CUDACC__)
 #define MPM_HD __host__ __device__
@@ -752,6 +753,65 @@ __device__ __forceinline__ void block_reduce_add(float (&v)[NV], double* dst, do
         double x = 0.0;
         for (int w = 0; w < nw; w++) x += sred[threadIdx.x * 32 + w];
         if (x != 0.0) atomicAdd(dst + threadIdx.x, x);
+    }
+}
+
+// one value per statistic: max (mode 1) or sum (mode 2) over the warp, then
+// FP64 atomics into dst[0..NV) by lane 0 (largest magnitude via the integer
+// order of non-negative doubles). All 32 lanes call it.
+template <int NV>
+__device__ __forceinline__ void warp_stat(int mode, float (&v)[NV], double* dst) {
+#pragma unroll
+    for (int k = 0; k < NV; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float w = __shfl_xor_sync(0xffffffffu, v[k], o);
+            v[k] = mode == 1 ? fmaxf(v[k], w) : v[k] + w;
+        }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            if (!(v[k] > 0.0f)) continue;
+            if (mode == 1)
+                atomicMax(reinterpret_cast<unsigned long long*>(dst + k),
+                          (unsigned long long)__double_as_longlong((double)v[k]));
+            else
+                atomicAdd(dst + k, (double)v[k]);
+        }
+}
+
+// a value's contribution to a statistic
+__device__ __forceinline__ float stat_of(int mode, float g) { return mode == 1 ? fabsf(g) : g * g; }
+
+// block version of warp_stat: one atomic per statistic and CTA. All threads
+// of the CTA call it; sred holds NV * 32 floats.
+template <int NV>
+__device__ __forceinline__ void block_stat(int mode, float (&v)[NV], double* dst, float* sred) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float w = __shfl_xor_sync(0xffffffffu, v[k], o);
+            v[k] = mode == 1 ? fmaxf(v[k], w) : v[k] + w;
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; k++) sred[k * 32 + warp] = v[k];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double x = 0.0;
+        for (int w = 0; w < nw; w++) {
+            const double y = sred[threadIdx.x * 32 + w];
+            x = mode == 1 ? fmax(x, y) : x + y;
+        }
+        if (x > 0.0) {
+            if (mode == 1)
+                atomicMax(reinterpret_cast<unsigned long long*>(dst + threadIdx.x),
+                          (unsigned long long)__double_as_longlong(x));
+            else
+                atomicAdd(dst + threadIdx.x, x);
+        }
     }
 }
 

@@ -503,8 +503,14 @@ __device__ __forceinline__ void g2p_bwd_scatter(const InstDev& I, const AdjArgs&
 __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A) {
     __shared__ TileSmem T;
     __shared__ InstDev sI;
+    __shared__ float sfac[2];
     const StepArgs& a = A.f;
     const int inst = a.chunk_inst[blockIdx.x];
+    if (A.gscale && threadIdx.x == 0) {
+        // regularisers of the x and v adjoints of state k+1 (Sec. III-E)
+        sfac[0] = (float)reg_factor(A.gscale, A.pstat_in[3 * inst + 0], A.oom, A.gdelta);
+        sfac[1] = (float)reg_factor(A.gscale, A.pstat_in[3 * inst + 1], A.oom, A.gdelta);
+    }
     const InstDev& I = stage_instance(sI, a.inst, inst);
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
     const bool active = p - I.pbeg < I.n;
@@ -529,6 +535,7 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A)
             gx[k] = A.adj[(kX + k) * N + p];
             float gv = A.adj[(kV + k) * N + p];
             if (a.clip > 0.f) { gx[k] = clipf(gx[k], a.clip); gv = clipf(gv, a.clip); }
+            if (A.gscale) { gx[k] *= sfac[0]; gv *= sfac[1]; }
             // adjoint of the advection x' = x + dt v'
             gvn[k] = gv + I.dt * gx[k];
         }
@@ -592,6 +599,7 @@ __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
     sincosf(P.psi, &sn, &cs);
     const long long base = I.node_off + (long long)lb * 64;
     float gp[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float st[3] = {0.f, 0.f, 0.f};   // statistics of v-bar after / before the contact and of m-bar
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int nd = lane + 32 * h;
@@ -625,12 +633,26 @@ __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
             dot = gv[0] * acc.y + gv[1] * acc.z + gv[2] * acc.w;
             float gm = -dot * inv_m * inv_m;
             if (a.clip > 0.f) gm = clipf(gm, a.clip);
+            if (A.gscale) {
+                // unregularised values; the P2G adjoint applies the factors
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    const float s0 = stat_of(A.gscale, g[d]), s1 = stat_of(A.gscale, gv[d]);
+                    st[0] = A.gscale == 1 ? fmaxf(st[0], s0) : st[0] + s0;
+                    st[1] = A.gscale == 1 ? fmaxf(st[1], s1) : st[1] + s1;
+                }
+                const float s2 = stat_of(A.gscale, gm);
+                st[2] = A.gscale == 1 ? fmaxf(st[2], s2) : st[2] + s2;
+            }
             out = make_float4(gm, gv[0] * inv_m, gv[1] * inv_m, gv[2] * inv_m);
         }
         A.gacc[base + nd] = out;
     }
+    if (A.gscale) warp_stat<3>(A.gscale, st, A.gstat + 3 * inst);
     if (I.shovel_on) {
         // warp sum of the pose adjoint in FP64, one atomic per value and warp
+        // (unregularised into gpose_raw when regularising: the host scales it)
+        double* dst = A.gscale ? A.gpose_raw : A.gpose;
         bool any = false;
 #pragma unroll
         for (int k = 0; k < 8; k++) any = any || (gp[k] != 0.f);
@@ -640,7 +662,7 @@ __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
                 float x = gp[k];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-                if (lane == 0 && x != 0.f) atomicAdd(A.gpose + 8 * inst + k, (double)x);
+                if (lane == 0 && x != 0.f) atomicAdd(dst + 8 * inst + k, (double)x);
             }
         }
     }
@@ -715,8 +737,8 @@ __device__ __forceinline__ float ld_again(const float* p) {
 // adjoint (m-bar, mv-bar) at the 27 nodes to gx (added), gv, the adjoint gA of
 // the affine matrix A = stress_scale tau + m_p C, and gmp (added).
 __device__ __forceinline__ void p2g_bwd_gather(const InstDev& I, const AdjArgs& A, const float (&x)[3],
-                                               const float (&v)[3], const float (&Am)[3][3], float (&gx)[3],
-                                               float (&gv)[3], float (&gA)[3][3], float& gmp) {
+                                               const float (&v)[3], const float (&Am)[3][3], float fm, float fv,
+                                               float (&gx)[3], float (&gv)[3], float (&gA)[3][3], float& gmp) {
     Stencil st;
     make_stencil(I, x, st);
     int ox[3], oy[3], oz[3];
@@ -726,8 +748,10 @@ __device__ __forceinline__ void p2g_bwd_gather(const InstDev& I, const AdjArgs& 
     // Per node: a = m_p v + Am d (hoisted over the loops), Wbar = m-bar m_p +
     // mv-bar . a, gx += Wbar grad W, gA += W mv-bar d^T. The terms of gx
     // through d = x_node - x_p sum to -Am^T S1 with S1 = sum W mv-bar, and
-    // gv, gmp follow from S1 and S0 = sum W m-bar after the loop.
+    // gv, gmp follow from S1 and S0 = sum W m-bar after the loop. The grid
+    // holds m-bar / fm and mv-bar / fv (fm = fv = 1 unless regularising).
     float S0 = 0.f, S1[3] = {0.f, 0.f, 0.f};
+    const float mpf = I.mp * fm;
 #pragma unroll
     for (int r = 0; r < 3; r++)
 #pragma unroll
@@ -751,9 +775,10 @@ __device__ __forceinline__ void p2g_bwd_gather(const InstDev& I, const AdjArgs& 
                 const float W = wxy * wz;
                 const float4 g = ga[lx.o[i] + oy[j] + oz[k]];
                 const float gm = g.x, gmv[3] = {g.y, g.z, g.w};
-                float Wbar = gm * I.mp;
+                float ma = 0.f;
 #pragma unroll
-                for (int r = 0; r < 3; r++) Wbar = fmaf(gmv[r], fmaf(Am[r][2], dzk, aij[r]), Wbar);
+                for (int r = 0; r < 3; r++) ma = fmaf(gmv[r], fmaf(Am[r][2], dzk, aij[r]), ma);
+                const float Wbar = fmaf(fv, ma, mpf * gm);
                 gx[0] = fmaf(Wbar, gwx * wz, gx[0]);
                 gx[1] = fmaf(Wbar, gwy * wz, gx[1]);
                 gx[2] = fmaf(Wbar, wxy * st.dw[2][k], gx[2]);
@@ -769,6 +794,13 @@ __device__ __forceinline__ void p2g_bwd_gather(const InstDev& I, const AdjArgs& 
             }
         }
     }
+    S0 *= fm;
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        S1[r] *= fv;
+#pragma unroll
+        for (int c = 0; c < 3; c++) gA[r][c] *= fv;
+    }
     gmp += S0 + S1[0] * v[0] + S1[1] * v[1] + S1[2] * v[2];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -780,7 +812,8 @@ __device__ __forceinline__ void p2g_bwd_gather(const InstDev& I, const AdjArgs& 
 // The chain through the trial F = (I + dt C) F and the stores of the
 // adjoint of state k (in place of the adjoint of state k+1).
 __device__ __forceinline__ void p2g_bwd_finish(const InstDev& I, const AdjArgs& A, long long p, const float (&gx)[3],
-                                               const float (&gv)[3], float (&gC)[3][3], const float (&gFt)[3][3]) {
+                                               const float (&gv)[3], float (&gC)[3][3], const float (&gFt)[3][3],
+                                               int mode, float (&st)[3]) {
     const StepArgs& a = A.f;
     const long long N = a.ncap;
     float C[3][3], F[3][3];
@@ -805,6 +838,11 @@ __device__ __forceinline__ void p2g_bwd_finish(const InstDev& I, const AdjArgs& 
         A.adj[(kX + k) * N + p] = gx[k];
         A.adj[(kV + k) * N + p] = gv[k];
         finite = finite && isfinite(gx[k]) && isfinite(gv[k]);
+        if (mode) {
+            const float sx = stat_of(mode, gx[k]), sv = stat_of(mode, gv[k]);
+            st[0] = mode == 1 ? fmaxf(st[0], sx) : st[0] + sx;
+            st[1] = mode == 1 ? fmaxf(st[1], sv) : st[1] + sv;
+        }
     }
 #pragma unroll
     for (int r = 0; r < 3; r++)
@@ -813,13 +851,17 @@ __device__ __forceinline__ void p2g_bwd_finish(const InstDev& I, const AdjArgs& 
             A.adj[(kC + 3 * r + c) * N + p] = gC[r][c];
             A.adj[(kF + 3 * r + c) * N + p] = gF[r][c];
             finite = finite && isfinite(gF[r][c]) && isfinite(gC[r][c]);
+            if (mode) {
+                const float sF = stat_of(mode, gF[r][c]);
+                st[2] = mode == 1 ? fmaxf(st[2], sF) : st[2] + sF;
+            }
         }
     if (!finite) atomicOr(a.status, kStatusNonFinite);
 }
 
 // gtau, gC (the affine part), gmp (the A : C part) and the clipped adjoint of F'
 __device__ __forceinline__ void p2g_bwd_affine(const InstDev& I, const AdjArgs& A, long long p, const float (&gA)[3][3],
-                                               float (&gFn)[3][3], float (&gtau)[3][3], float (&gC)[3][3],
+                                               float fF, float (&gFn)[3][3], float (&gtau)[3][3], float (&gC)[3][3],
                                                float& gmp) {
     const StepArgs& a = A.f;
     const long long N = a.ncap;
@@ -828,7 +870,7 @@ __device__ __forceinline__ void p2g_bwd_affine(const InstDev& I, const AdjArgs& 
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             const float g = ld_again(A.adj + (kF + 3 * r + c) * N + p);
-            gFn[r][c] = a.clip > 0.f ? clipf(g, a.clip) : g;
+            gFn[r][c] = (a.clip > 0.f ? clipf(g, a.clip) : g) * fF;
             gtau[r][c] = I.stress_scale * gA[r][c];
             gC[r][c] = I.mp * gA[r][c];
             gmp += gA[r][c] * ld_again(a.sin + (kC + 3 * r + c) * N + p);
@@ -839,17 +881,38 @@ __device__ __forceinline__ void p2g_bwd_affine(const InstDev& I, const AdjArgs& 
 // Adjoint of P2G and of the constitutive step, FP32. A particle whose
 // deformation is ill-conditioned for FP32 (see needs_fp64) is left untouched
 // and listed for k_p2g_bwd_fp64.
-__global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd(AdjArgs A) {
+// regulariser factors of a P2G-adjoint CTA (Sec. III-E): F-bar of state
+// k+1, and m-bar / mv-bar of the grid; ones when not regularising
+__device__ __forceinline__ void p2g_bwd_factors(const AdjArgs& A, int inst, float* f) {
+    if (!A.gscale) {
+        f[0] = f[1] = f[2] = 1.0f;
+        return;
+    }
+    float s0;
+    f[0] = (float)reg_factor(A.gscale, A.pstat_in[3 * inst + 2], A.oom, A.gdelta);
+    reg_grid_factors(A.gscale, A.gstat + 3 * inst, A.oom, A.gdelta, s0, f[1], f[2]);
+}
+
+// The P2G adjoint of one CTA; Reg: with the regularisers of Sec. III-E (a
+// separate instantiation, so that the plain path carries none of their code).
+template <bool Reg>
+__device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A) {
     __shared__ double sred[4 * 32];
     __shared__ InstDev sI;
     __shared__ float sS[kParked * kChunk];
+    __shared__ float sfac[3];   // F-bar, m-bar, mv-bar factors
     const StepArgs& a = A.f;
     const int inst = a.chunk_inst[blockIdx.x];
+    if (threadIdx.x == 0) {
+        if (Reg) p2g_bwd_factors(A, inst, sfac);
+        else sfac[0] = sfac[1] = sfac[2] = 1.0f;
+    }
     const InstDev& I = stage_instance(sI, a.inst, inst);
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
     const bool active = p - I.pbeg < I.n;
     const long long N = a.ncap;
     float gmu = 0.f, glam = 0.f, galpha = 0.f, gmp = 0.f;
+    float st[3] = {0.f, 0.f, 0.f};   // statistics of the x, v, F adjoints of state k
     if (active) {
         float x[3], v[3], gx[3];
 #pragma unroll
@@ -880,19 +943,27 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd(AdjArgs A)
             a.fb_list[atomicAdd(a.fb_count, 1)] = (int)p;
         } else {
             float gv[3], gA[3][3];
-            p2g_bwd_gather(I, A, x, v, Am, gx, gv, gA, gmp);
+            p2g_bwd_gather(I, A, x, v, Am, Reg ? sfac[1] : 1.0f, Reg ? sfac[2] : 1.0f, gx, gv, gA, gmp);
             float gFn[3][3], gtau[3][3], gC[3][3], gFt[3][3];
-            p2g_bwd_affine(I, A, p, gA, gFn, gtau, gC, gmp);
+            p2g_bwd_affine(I, A, p, gA, Reg ? sfac[0] : 1.0f, gFn, gtau, gC, gmp);
             Spectral<float> S;
             unpark(sS, S, I.smin);
             constitutive_adjoint_spectral<float>(S, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, gFt, gmu, glam,
                                                  galpha);
-            p2g_bwd_finish(I, A, p, gx, gv, gC, gFt);
+            p2g_bwd_finish(I, A, p, gx, gv, gC, gFt, Reg ? A.gscale : 0, st);
         }
     }
     float gd[4] = {gmu, glam, galpha, gmp};
     block_reduce_add<4>(gd, A.gmat + 4 * inst, sred);
+    if (Reg) {
+        __syncthreads();   // sred is reused
+        block_stat<3>(A.gscale, st, A.pstat_out + 3 * inst, reinterpret_cast<float*>(sred));
+    }
 }
+
+__global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd(AdjArgs A) { p2g_bwd_cta<false>(A); }
+
+__global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd_reg(AdjArgs A) { p2g_bwd_cta<true>(A); }
 
 // The particles k_p2g_bwd listed: the same adjoint with the SVD, the return
 // mapping and their adjoint in FP64.
@@ -918,12 +989,23 @@ __global__ void __launch_bounds__(kFp64Threads) k_p2g_bwd_fp64(AdjArgs A) {
         for (int r = 0; r < 3; r++)
 #pragma unroll
             for (int c = 0; c < 3; c++) Am[r][c] = I.stress_scale * tau[r][c] + I.mp * C[r][c];
+        float fac[3], st[3] = {0.f, 0.f, 0.f};
+        p2g_bwd_factors(A, inst, fac);
         float gv[3], gA[3][3], gmp = 0.f, gmu = 0.f, glam = 0.f, galpha = 0.f;
-        p2g_bwd_gather(I, A, x, v, Am, gx, gv, gA, gmp);
+        p2g_bwd_gather(I, A, x, v, Am, fac[1], fac[2], gx, gv, gA, gmp);
         float gFn[3][3], gtau[3][3], gC[3][3], gFt[3][3];
-        p2g_bwd_affine(I, A, p, gA, gFn, gtau, gC, gmp);
+        p2g_bwd_affine(I, A, p, gA, fac[0], gFn, gtau, gC, gmp);
         constitutive_adjoint_fp64(Ft, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, tau, gFt, gmu, glam, galpha);
-        p2g_bwd_finish(I, A, p, gx, gv, gC, gFt);
+        p2g_bwd_finish(I, A, p, gx, gv, gC, gFt, A.gscale, st);
+        if (A.gscale)
+            for (int k = 0; k < 3; k++) {
+                if (!(st[k] > 0.0f)) continue;
+                if (A.gscale == 1)
+                    atomicMax(reinterpret_cast<unsigned long long*>(A.pstat_out + 3 * inst + k),
+                              (unsigned long long)__double_as_longlong((double)st[k]));
+                else
+                    atomicAdd(A.pstat_out + 3 * inst + k, (double)st[k]);
+            }
         atomicAdd(A.gmat + 4 * inst + 0, (double)gmu);
         atomicAdd(A.gmat + 4 * inst + 1, (double)glam);
         atomicAdd(A.gmat + 4 * inst + 2, (double)galpha);
@@ -1179,6 +1261,26 @@ __global__ void __launch_bounds__(kChunk) k_unpermute(const InstDev* inst, const
     for (int c = 0; c < kStateComps; c++) dst[c * ncap + p] = src[c * ncap + q];
 }
 
+// statistics (Sec. III-E) of the x, v and F adjoints of a state (the loss
+// seed of a backward): largest magnitude (mode 1) or sum of squares (2)
+__global__ void __launch_bounds__(kChunk) k_adj_stats(const InstDev* inst, const int* chunk_inst, long long ncap,
+                                                      const float* adj, int mode, double* pstat) {
+    __shared__ float sred[3 * 32];
+    const int i = chunk_inst[blockIdx.x];
+    const InstDev& I = inst[i];
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    float st[3] = {0.f, 0.f, 0.f};
+    if (p - I.pbeg < I.n) {
+        for (int c = 0; c < kStateComps; c++) {
+            const int which = c < kV ? 0 : (c < kC ? 1 : (c < kF ? -1 : 2));
+            if (which < 0) continue;
+            const float s = stat_of(mode, adj[c * ncap + p]);
+            st[which] = mode == 1 ? fmaxf(st[which], s) : st[which] + s;
+        }
+    }
+    block_stat<3>(mode, st, pstat + 3 * i, sred);
+}
+
 }  // namespace mpm
 
 // ---------------------------------------------------------------------------
@@ -1202,7 +1304,8 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
         case KernelId::GridBwd: k_grid_bwd<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
         case KernelId::P2GBwd:
             if (!a.spec) return cudaErrorInvalidValue;   // needs the recorded SVD
-            k_p2g_bwd<<<a.n_chunks, kChunk, 0, s>>>(A);
+            if (A.gscale) k_p2g_bwd_reg<<<a.n_chunks, kChunk, 0, s>>>(A);
+            else k_p2g_bwd<<<a.n_chunks, kChunk, 0, s>>>(A);
             break;
         case KernelId::GridClear: k_grid_clear<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
         case KernelId::P2GFp64: k_p2g_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(a); break;
@@ -1215,6 +1318,13 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
         }
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_stats(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap,
+                             const float* adj, int mode, double* pstat, cudaStream_t st) {
+    if (n_chunks <= 0 || !mode) return cudaSuccess;
+    k_adj_stats<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, ncap, adj, mode, pstat);
     return cudaGetLastError();
 }
 

@@ -16,6 +16,11 @@ constexpr int kFp64Threads = 128;
 cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s);
 cudaError_t launch_state_from_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* x,
                                   const float* v, const float* C, const float* F, float* s, cudaStream_t st);
+// statistics of the x, v, F adjoints of a state for the regularisers of
+// Sec. III-E (mode 1: largest magnitude, 2: sum of squares) into
+// pstat[3 * instance + {0, 1, 2}] (zeroed by the caller)
+cudaError_t launch_adj_stats(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap,
+                             const float* adj, int mode, double* pstat, cudaStream_t st);
 cudaError_t launch_adj_from_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* gx,
                                 const float* gv, float* adj, cudaStream_t st);
 cudaError_t launch_state_to_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* s, float* x,

@@ -76,6 +76,16 @@ struct AdjArgs {
     float4* gacc;           // grid adjoint buffer (zero on entry for touched blocks)
     double* gmat;           // n_inst * 4: d/d(mu, lambda, alpha, m_p)
     double* gpose;          // n_inst * 8: adjoint of this substep's pose
+    // Sec. III-E regularisers of whole adjoint vectors (gscale 1: dynamic
+    // scaling, 2: normalisation; 0: off). Statistics per instance are the
+    // largest magnitude (1) or the sum of squares (2) of a vector.
+    int gscale;
+    float oom, gdelta;
+    const double* pstat_in; // n_inst * 3: x, v, F adjoints of state k+1
+    double* pstat_out;      // n_inst * 3: the same of state k (zeroed by the host)
+    double* gstat;          // n_inst * 3: grid v-bar after / before the contact, m-bar of substep k,
+                            // unregularised (zeroed by the host)
+    double* gpose_raw;      // n_inst * 8: the grid kernel's pose adjoint, unregularised
 };
 
 }  // namespace mpm

@@ -5,11 +5,11 @@ import numpy as np
 import oracle
 
 
-def oracle_params(w, particle_collision=1, shovel_on=1, clip=0, gravity=None):
+def oracle_params(w, particle_collision=1, shovel_on=1, clip=0, gravity=None, grad_scale=0):
     return oracle.Params(res=tuple(w.res), dx=w.dx, dt=w.dt, gravity=tuple(w.gravity if gravity is None else gravity),
                          bound=w.bound, E=w.E, nu=w.nu, rho=w.rho, phi_deg=w.phi_deg, vol=w.vol, friction=w.friction,
                          particle_collision=particle_collision, shovel_half=tuple(w.shovel_half), shovel_on=shovel_on,
-                         clip_grads=clip)
+                         clip_grads=clip, grad_scale=grad_scale)
 
 
 def oracle_actions(w):

@@ -65,6 +65,9 @@ def test_invalid_arguments_are_rejected(L):
     assert _create(L, good, mat, np.array([[0.5, 0.01, 0.5]], np.float32)) == -4
     assert _create(L, good, mat, np.array([[0.5, np.nan, 0.5]], np.float32)) == -1
     assert _create(L, good, mat, x, mpm.make_options(checkpoint_every=0)) == -1
+    assert _create(L, good, mat, x, mpm.make_options(grad_scale=3)) == -1            # no such regulariser
+    assert _create(L, good, mat, x, mpm.make_options(grad_scale=1, clip_grads=1)) == -1   # one at a time
+    assert _create(L, good, mat, x, mpm.make_options(grad_scale=2, grad_delta=0.0)) == -1
     h = ctypes.c_void_p()
     assert L.mpm_create(0, None, None, None, None, None, ctypes.byref(h)) == -1
     # NULL handles

