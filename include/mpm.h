@@ -101,6 +101,9 @@ typedef struct {
                                * Not together with clip_grads. */
     double oom_star;          /* [4] */
     double grad_delta;        /* [1e-6] */
+    int fuse_adjoint;         /* [1] run the P2G adjoint of a substep and the G2P adjoint of the one
+                               * before it in one pass over the particles where both lie in the same
+                               * recorded segment (not with grad_scale or tile_scatter) */
 } mpm_options;
 
 /* Digging skill (Sec. III-B): theta = (displace, rotate, insert_dist,
@@ -268,13 +271,15 @@ int mpm_set_substep(mpm_handle* h, int64_t substep);
 /* Kernel timing: enable != 0 records a CUDA event pair around every kernel
  * launch on the handle's stream (counters reset on every call). Kernel ids:
  * 0 k_p2g, 1 k_grid, 2 k_g2p, 3 k_g2p_bwd, 4 k_grid_bwd, 5 k_p2g_bwd,
- * 6 k_grid_clear, 7 k_slot_clear, 8 k_p2g_fp64, 9 k_p2g_bwd_fp64 (ids below
- * MPM_PROFILE_KERNELS). The two _fp64 kernels redo, in FP64, the particles
- * whose deformation gradient is too ill-conditioned for the FP32 SVD; they
- * launch every substep and return at once when there are none.
+ * 6 k_grid_clear, 7 k_slot_clear, 8 k_p2g_fp64, 9 k_p2g_bwd_fp64,
+ * 10 k_p2g_g2p_bwd, 11 k_p2g_g2p_bwd_fp64 (ids below MPM_PROFILE_KERNELS).
+ * The _fp64 kernels redo, in FP64, the particles whose deformation gradient
+ * is too ill-conditioned for the FP32 SVD; they launch every substep and
+ * return at once when there are none. k_p2g_g2p_bwd is the fused adjoint
+ * (option fuse_adjoint).
  * mpm_profile_read waits for the recorded events and gives the summed device
  * time (ms) and the launch count of one kernel. */
-#define MPM_PROFILE_KERNELS 10
+#define MPM_PROFILE_KERNELS 12
 int mpm_profile(mpm_handle* h, int enable);
 int mpm_profile_read(mpm_handle* h, int kernel, double* total_ms, int64_t* launches);
 const char* mpm_kernel_name(int kernel);

@@ -170,7 +170,7 @@ struct mpm_handle {
     std::vector<char> seg_dirty;      // grid slot k holds accumulators/flags to clear
     int64_t seg_valid = -1;           // segment whose states/grids the slots hold
     int seg_valid_len = 0;
-    DevBuf<float4> d_gacc;
+    DevBuf<float4> d_gacc, d_gacc2;   // grid adjoint; the second for the fused adjoint
     bool gacc_dirty = true;
     DevBuf<float> d_adj;
     DevBuf<double> d_gmat, d_gpose;
@@ -507,6 +507,21 @@ int run_kernel(mpm_handle* h, KernelId id, const AdjArgs& A) {
     return MPM_OK;
 }
 
+int run_fused(mpm_handle* h, KernelId id, const AdjArgs& A, const AdjArgs& G) {
+    if (h->prof.on) {
+        Profiler::Pending p{(int)id, h->prof.get(), h->prof.get()};
+        CK(cudaEventRecord(p.a, h->stream));
+        CK(launch_fused(id, A, G, h->stream));
+        CK(cudaEventRecord(p.b, h->stream));
+        h->prof.pending.push_back(p);
+        if (h->prof.pending.size() > 65536) h->prof.flush();
+    } else {
+        CK(launch_fused(id, A, G, h->stream));
+    }
+    h->launches++;
+    return MPM_OK;
+}
+
 int run_substep(mpm_handle* h, const StepArgs& a) {
     AdjArgs A;
     std::memset(&A, 0, sizeof A);
@@ -678,6 +693,7 @@ int mpm_create(int n_inst, const mpm_config* cfgs, const mpm_material* mats, con
     h->opt.grad_scale = 0;
     h->opt.oom_star = 4.0;
     h->opt.grad_delta = 1e-6;
+    h->opt.fuse_adjoint = 1;
     if (opts) h->opt = *opts;
     h->tile_scatter = h->opt.tile_scatter ? 1 : 0;
     h->n_ext = n_ext;
@@ -771,7 +787,7 @@ void mpm_destroy(mpm_handle* h) {
     for (auto& b : h->seg_vout) b.release();
     for (auto& b : h->seg_flags) b.release();
     for (auto& b : h->seg_spec) b.release();
-    h->d_gacc.release();
+    h->d_gacc.release(); h->d_gacc2.release();
     h->d_adj.release(); h->d_gmat.release(); h->d_gpose.release();
     h->d_pstat.release(); h->d_gstat.release(); h->d_gpose_raw.release();
     h->d_state2.release(); h->d_adj2.release(); h->d_ext2.release(); h->d_key.release(); h->d_rank.release();
@@ -1139,7 +1155,11 @@ static int backward_launch(mpm_handle* h, const float* gx, const float* gv, bool
     const int n_inst = (int)h->inst.size();
     const size_t state_floats = (size_t)h->ncap * kStateComps;
     cudaStream_t s = h->stream;
-    if (fresh_gacc || h->gacc_dirty) CK(cudaMemsetAsync(h->d_gacc.p, 0, h->d_gacc.n * sizeof(float4), s));
+    const bool fuse = h->opt.fuse_adjoint && !h->opt.grad_scale && !h->tile_scatter;
+    if (fresh_gacc || h->gacc_dirty) {
+        CK(cudaMemsetAsync(h->d_gacc.p, 0, h->d_gacc.n * sizeof(float4), s));
+        if (h->d_gacc2.p) CK(cudaMemsetAsync(h->d_gacc2.p, 0, h->d_gacc2.n * sizeof(float4), s));
+    }
     h->gacc_dirty = true;   // until every reversed substep has cleared its blocks
     CK(launch_adj_from_ext(h->ncap, h->ncap, h->d_ext_of_slot.p, gx, gv, h->d_adj.p, s));
     h->launches++;
@@ -1168,14 +1188,17 @@ static int backward_launch(mpm_handle* h, const float* gx, const float* gv, bool
             h->seg_valid = j;
             h->seg_valid_len = seg_len;
         }
-        // reverse it
-        for (int i = seg_len - 1; i >= 0; i--) {
+        // reverse it; with fusion, the P2G adjoint of substep i and the G2P
+        // adjoint of substep i-1 run as one kernel (grid adjoints ping-pong
+        // between two buffers), so only the segment's last substep runs its
+        // G2P adjoint alone and its first its P2G adjoint alone
+        auto args = [&](int i, float4* gacc) {
             AdjArgs A;
             std::memset(&A, 0, sizeof A);
             A.f = slot_args(h, i, h->rec_start + seg_begin + i);
             A.f.sout = h->seg_state[i].p;
             A.adj = h->d_adj.p;
-            A.gacc = h->d_gacc.p;
+            A.gacc = gacc;
             A.gmat = h->d_gmat.p;
             A.gpose = h->d_gpose.p + (size_t)(seg_begin + i) * n_inst * 8;
             if (gscale) {
@@ -1188,7 +1211,25 @@ static int backward_launch(mpm_handle* h, const float* gx, const float* gv, bool
                 A.gstat = h->d_gstat.p + r * n_inst * 3;
                 A.gpose_raw = h->d_gpose_raw.p + r * n_inst * 8;
             }
-            RK(run_adjoint_substep(h, A));
+            return A;
+        };
+        float4* gcur = h->d_gacc.p;
+        float4* goth = h->d_gacc2.p;
+        for (int i = seg_len - 1; i >= 0; i--) {
+            const AdjArgs A = args(i, gcur);
+            if (!fuse || i == seg_len - 1) RK(run_kernel(h, KernelId::G2PBwd, A));
+            RK(run_kernel(h, KernelId::GridBwd, A));
+            if (fuse && i > 0) {
+                const AdjArgs G = args(i - 1, goth);
+                RK(run_fused(h, KernelId::P2GG2PBwd, A, G));
+                RK(run_fused(h, KernelId::P2GG2PBwdFp64, A, G));
+                RK(run_kernel(h, KernelId::GridClear, A));
+                std::swap(gcur, goth);
+            } else {
+                RK(run_kernel(h, KernelId::P2GBwd, A));
+                RK(run_kernel(h, KernelId::P2GBwdFp64, A));
+                RK(run_kernel(h, KernelId::GridClear, A));
+            }
             h->seg_dirty[i] = 0;
         }
         h->seg_valid = -1;
@@ -1249,8 +1290,10 @@ int mpm_backward(mpm_handle* h, const float* dL_dx, const float* dL_dv, int devi
     RK(set_device(h));
     const int n_inst = (int)h->inst.size();
     const size_t state_floats = (size_t)h->ncap * kStateComps;
-    const bool fresh_gacc = h->d_gacc.n < (size_t)h->n_nodes;
+    const bool fresh_gacc = h->d_gacc.n < (size_t)h->n_nodes ||
+                            (h->opt.fuse_adjoint && h->d_gacc2.n < (size_t)h->n_nodes);
     RK(h->d_gacc.ensure((size_t)h->n_nodes, h->device_bytes));
+    if (h->opt.fuse_adjoint) RK(h->d_gacc2.ensure((size_t)h->n_nodes, h->device_bytes));
     RK(h->d_adj.ensure(state_floats, h->device_bytes));
     RK(h->d_gmat.ensure((size_t)n_inst * 4, h->device_bytes));
     RK(h->d_gpose.ensure((size_t)h->rec_len * n_inst * 8, h->device_bytes));
@@ -1495,7 +1538,7 @@ int mpm_profile_read(mpm_handle* h, int kernel, double* total_ms, int64_t* launc
 const char* mpm_kernel_name(int kernel) {
     static const char* names[] = {"k_p2g",     "k_grid",       "k_g2p",       "k_g2p_bwd",
                                   "k_grid_bwd", "k_p2g_bwd", "k_grid_clear", "k_slot_clear",
-                                  "k_p2g_fp64", "k_p2g_bwd_fp64"};
+                                  "k_p2g_fp64", "k_p2g_bwd_fp64", "k_p2g_g2p_bwd", "k_p2g_g2p_bwd_fp64"};
     if (kernel < 0 || kernel >= (int)KernelId::Count) return "";
     return names[kernel];
 }

@@ -34,6 +34,9 @@
 #ifndef MPM_MINB_P2G_BWD
 #define MPM_MINB_P2G_BWD 3
 #endif
+#ifndef MPM_MINB_FUSED_BWD
+#define MPM_MINB_FUSED_BWD 3
+#endif
 
 namespace mpm {
 
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
 // Sv = sum W v_node (velocities of the grid vg).
 __device__ __forceinline__ void g2p_bwd_scatter(const InstDev& I, const AdjArgs& A, const Stencil& st,
                                                 const int (&ox)[3], const int (&oy)[3], const int (&oz)[3],
-                                                const float4* vg, TileSmem& T, const float (&gvn)[3],
+                                                const float4* vg, TileSmem* T, const float (&gvn)[3],
                                                 const float (&gC)[3][3], float (&gx)[3]) {
     const float kap = 4.0f * I.inv_dx * I.inv_dx;
     float kgC[3][3];
@@ -484,8 +487,9 @@ __device__ __forceinline__ void g2p_bwd_scatter(const InstDev& I, const AdjArgs&
                 float b[3];
 #pragma unroll
                 for (int r = 0; r < 3; r++) b[r] = fmaf(kgC[r][2], dzk, bij[r]);
-                tile_add(T, ga, lx.o[i] + oy[j] + oz[k], st, i, j, k,
-                         make_float4(W * b[0], W * b[1], W * b[2], 0.f), 3);
+                const float4 contrib = make_float4(W * b[0], W * b[1], W * b[2], 0.f);
+                if (T) tile_add(*T, ga, lx.o[i] + oy[j] + oz[k], st, i, j, k, contrib, 3);
+                else atomicAdd(ga + lx.o[i] + oy[j] + oz[k], contrib);
                 const float Wbar = g.x * b[0] + g.y * b[1] + g.z * b[2];
                 gx[0] = fmaf(Wbar, gwx * wz, gx[0]);
                 gx[1] = fmaf(Wbar, gwy * wz, gx[1]);
@@ -577,7 +581,7 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A)
         for (int r = 0; r < 3; r++)
 #pragma unroll
             for (int c = 0; c < 3; c++) gC[r][c] = A.adj[(kC + 3 * r + c) * N + p];
-        g2p_bwd_scatter(I, A, st, ox, oy, oz, vg, T, gvn, gC, gx);
+        g2p_bwd_scatter(I, A, st, ox, oy, oz, vg, &T, gvn, gC, gx);
 #pragma unroll
         for (int k = 0; k < 3; k++) A.adj[(kX + k) * N + p] = gx[k];
     }
@@ -811,6 +815,10 @@ __device__ __forceinline__ void p2g_bwd_gather(const InstDev& I, const AdjArgs& 
 
 // The chain through the trial F = (I + dt C) F and the stores of the
 // adjoint of state k (in place of the adjoint of state k+1).
+// (Store: every component of the adjoint of state k, or, when the caller
+// goes on with the G2P adjoint of the substep before, F-bar only; gC leaves
+// with the chain term added.)
+template <bool Store = true>
 __device__ __forceinline__ void p2g_bwd_finish(const InstDev& I, const AdjArgs& A, long long p, const float (&gx)[3],
                                                const float (&gv)[3], float (&gC)[3][3], const float (&gFt)[3][3],
                                                int mode, float (&st)[3]) {
@@ -835,8 +843,10 @@ __device__ __forceinline__ void p2g_bwd_finish(const InstDev& I, const AdjArgs& 
     bool finite = true;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        A.adj[(kX + k) * N + p] = gx[k];
-        A.adj[(kV + k) * N + p] = gv[k];
+        if (Store) {
+            A.adj[(kX + k) * N + p] = gx[k];
+            A.adj[(kV + k) * N + p] = gv[k];
+        }
         finite = finite && isfinite(gx[k]) && isfinite(gv[k]);
         if (mode) {
             const float sx = stat_of(mode, gx[k]), sv = stat_of(mode, gv[k]);
@@ -848,7 +858,7 @@ __device__ __forceinline__ void p2g_bwd_finish(const InstDev& I, const AdjArgs& 
     for (int r = 0; r < 3; r++)
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            A.adj[(kC + 3 * r + c) * N + p] = gC[r][c];
+            if (Store) A.adj[(kC + 3 * r + c) * N + p] = gC[r][c];
             A.adj[(kF + 3 * r + c) * N + p] = gF[r][c];
             finite = finite && isfinite(gF[r][c]) && isfinite(gC[r][c]);
             if (mode) {
@@ -893,10 +903,81 @@ __device__ __forceinline__ void p2g_bwd_factors(const AdjArgs& A, int inst, floa
     reg_grid_factors(A.gscale, A.gstat + 3 * inst, A.oom, A.gdelta, s0, f[1], f[2]);
 }
 
+// The G2P adjoint of one particle for the substep of G, given the adjoints
+// of the particle's x, v, C after that substep in registers (the second half
+// of the fused adjoint): advection, particle contact (pose sums per warp when
+// warp_uniform, all lanes calling; else per thread), scatter into G.gacc with
+// global atomics, and the partial x-bar of the state before it into G.adj.
+__device__ __forceinline__ void g2p_bwd_particle(const InstDev& I, const AdjArgs& G, int inst, long long p,
+                                                 bool active, bool warp_uniform, const float (&gx_in)[3],
+                                                 const float (&gv_in)[3], const float (&gC)[3][3]) {
+    const StepArgs& a = G.f;
+    const long long N = a.ncap;
+    float x[3] = {0.5f, 0.5f, 0.5f};
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) x[k] = ld(a.sin, N, kX + k, p);
+    }
+    Stencil st;
+    make_stencil(I, x, st);
+    int ox[3], oy[3], oz[3];
+    node_offsets(I, st, ox, oy, oz);
+    const float4* vg = a.vout + I.node_off;
+    float gx[3], gvn[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        gx[k] = a.clip > 0.f ? clipf(gx_in[k], a.clip) : gx_in[k];
+        const float gv = a.clip > 0.f ? clipf(gv_in[k], a.clip) : gv_in[k];
+        gvn[k] = gv + I.dt * gx[k];   // adjoint of the advection x' = x + dt v'
+    }
+    if (I.pcoll && I.shovel_on) {
+        float gp[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool contact = false;
+        if (active) {
+            const Pose P = load_pose(I, a.substep);
+            float sn, cs, n[3], nl[3];
+            sincosf(P.psi, &sn, &cs);
+            if (shovel_inside(I, P, cs, sn, x, n, nl)) {
+                contact = true;
+                float v[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < 3; i++)
+#pragma unroll
+                    for (int j = 0; j < 3; j++)
+#pragma unroll
+                        for (int k = 0; k < 3; k++) {
+                            const float W = st.w[0][i] * st.w[1][j] * st.w[2][k];
+                            const float4 g = __ldg(vg + ox[i] + oy[j] + oz[k]);
+                            v[0] += W * g.x; v[1] += W * g.y; v[2] += W * g.z;
+                        }
+                float g0[3] = {gvn[0], gvn[1], gvn[2]}, gq[3] = {0.f, 0.f, 0.f};
+                gvn[0] = gvn[1] = gvn[2] = 0.f;
+                shovel_project_adj(I, P, cs, sn, x, v, g0, gvn, gq, gp);
+                gx[0] += gq[0]; gx[1] += gq[1]; gx[2] += gq[2];
+            }
+        }
+        if (warp_uniform) {
+            warp_reduce_add<8>(gp, G.gpose + 8 * inst, contact);
+        } else if (contact) {
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                if (gp[k] != 0.f) atomicAdd(G.gpose + 8 * inst + k, (double)gp[k]);
+        }
+    }
+    if (active) {
+        g2p_bwd_scatter(I, G, st, ox, oy, oz, vg, nullptr, gvn, gC, gx);
+#pragma unroll
+        for (int k = 0; k < 3; k++) G.adj[(kX + k) * N + p] = gx[k];
+    }
+}
+
 // The P2G adjoint of one CTA; Reg: with the regularisers of Sec. III-E (a
 // separate instantiation, so that the plain path carries none of their code).
-template <bool Reg>
-__device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A) {
+// Fused: G is the G2P adjoint of the substep before, which this CTA runs
+// for its particles right after (g2p_bwd_particle), instead of storing their
+// x, v, C adjoints.
+template <bool Reg, bool Fused>
+__device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A, const AdjArgs* G) {
     __shared__ double sred[4 * 32];
     __shared__ InstDev sI;
     __shared__ float sS[kParked * kChunk];
@@ -913,6 +994,9 @@ __device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A) {
     const long long N = a.ncap;
     float gmu = 0.f, glam = 0.f, galpha = 0.f, gmp = 0.f;
     float st[3] = {0.f, 0.f, 0.f};   // statistics of the x, v, F adjoints of state k
+    // fused: the x, v, C adjoints of state k for the G2P adjoint of substep k-1
+    float gxk[3] = {0.f, 0.f, 0.f}, gvk[3] = {0.f, 0.f, 0.f}, gCk[3][3] = {{0.f}};
+    bool go_on = false;
     if (active) {
         float x[3], v[3], gx[3];
 #pragma unroll
@@ -950,9 +1034,19 @@ __device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A) {
             unpark(sS, S, I.smin);
             constitutive_adjoint_spectral<float>(S, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, gFt, gmu, glam,
                                                  galpha);
-            p2g_bwd_finish(I, A, p, gx, gv, gC, gFt, Reg ? A.gscale : 0, st);
+            p2g_bwd_finish<!Fused>(I, A, p, gx, gv, gC, gFt, Reg ? A.gscale : 0, st);
+            if (Fused) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) { gxk[k] = gx[k]; gvk[k] = gv[k]; }
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++) gCk[r][c] = gC[r][c];
+                go_on = true;
+            }
         }
     }
+    if (Fused) g2p_bwd_particle(I, *G, inst, p, go_on, true, gxk, gvk, gCk);
     float gd[4] = {gmu, glam, galpha, gmp};
     block_reduce_add<4>(gd, A.gmat + 4 * inst, sred);
     if (Reg) {
@@ -961,13 +1055,26 @@ __device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A) {
     }
 }
 
-__global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd(AdjArgs A) { p2g_bwd_cta<false>(A); }
+__global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd(AdjArgs A) {
+    p2g_bwd_cta<false, false>(A, nullptr);
+}
 
-__global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd_reg(AdjArgs A) { p2g_bwd_cta<true>(A); }
+__global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd_reg(AdjArgs A) {
+    p2g_bwd_cta<true, false>(A, nullptr);
+}
+
+// the P2G adjoint of substep k (A) and the G2P adjoint of substep k-1 (G) in
+// one pass over the particles: the x, v, C adjoints of state k stay in
+// registers. G.gacc is the other grid-adjoint buffer (zero on entry).
+__global__ void __launch_bounds__(kChunk, MPM_MINB_FUSED_BWD) k_p2g_g2p_bwd(AdjArgs A, AdjArgs G) {
+    p2g_bwd_cta<false, true>(A, &G);
+}
 
 // The particles k_p2g_bwd listed: the same adjoint with the SVD, the return
-// mapping and their adjoint in FP64.
-__global__ void __launch_bounds__(kFp64Threads) k_p2g_bwd_fp64(AdjArgs A) {
+// mapping and their adjoint in FP64; Fused: then the G2P adjoint of the
+// substep before (G) for them, as k_p2g_g2p_bwd does for the others.
+template <bool Fused>
+__device__ __forceinline__ void p2g_bwd_fp64_all(const AdjArgs& A, const AdjArgs* G) {
     __shared__ int scount;
     const StepArgs& a = A.f;
     const int count = fb_begin(a.fb_count, &scount);
@@ -996,7 +1103,8 @@ __global__ void __launch_bounds__(kFp64Threads) k_p2g_bwd_fp64(AdjArgs A) {
         float gFn[3][3], gtau[3][3], gC[3][3], gFt[3][3];
         p2g_bwd_affine(I, A, p, gA, fac[0], gFn, gtau, gC, gmp);
         constitutive_adjoint_fp64(Ft, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, tau, gFt, gmu, glam, galpha);
-        p2g_bwd_finish(I, A, p, gx, gv, gC, gFt, A.gscale, st);
+        p2g_bwd_finish<!Fused>(I, A, p, gx, gv, gC, gFt, A.gscale, st);
+        if (Fused) g2p_bwd_particle(I, *G, inst, p, true, false, gx, gv, gC);
         if (A.gscale)
             for (int k = 0; k < 3; k++) {
                 if (!(st[k] > 0.0f)) continue;
@@ -1013,6 +1121,12 @@ __global__ void __launch_bounds__(kFp64Threads) k_p2g_bwd_fp64(AdjArgs A) {
         atomicAdd(a.fp64_count, 1ull);
     }
     fb_end(a.fb_count);
+}
+
+__global__ void __launch_bounds__(kFp64Threads) k_p2g_bwd_fp64(AdjArgs A) { p2g_bwd_fp64_all<false>(A, nullptr); }
+
+__global__ void __launch_bounds__(kFp64Threads) k_p2g_g2p_bwd_fp64(AdjArgs A, AdjArgs G) {
+    p2g_bwd_fp64_all<true>(A, &G);
 }
 
 __global__ void __launch_bounds__(256) k_grid_clear(AdjArgs A) {
@@ -1310,12 +1424,26 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
         case KernelId::GridClear: k_grid_clear<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
         case KernelId::P2GFp64: k_p2g_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(a); break;
         case KernelId::P2GBwdFp64: k_p2g_bwd_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(A); break;
+        case KernelId::P2GG2PBwd:
+        case KernelId::P2GG2PBwdFp64: return cudaErrorInvalidValue;   // two argument sets: launch_fused
         case KernelId::SlotClear: {
             AdjArgs C = A;
             C.gacc = nullptr;
             k_grid_clear<<<grid_ctas(a.n_blocks), 256, 0, s>>>(C);
             break;
         }
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(KernelId id, const AdjArgs& A, const AdjArgs& G, cudaStream_t s) {
+    const StepArgs& a = A.f;
+    if (a.n_chunks <= 0) return cudaSuccess;
+    if (!a.spec || A.gscale || a.tile) return cudaErrorInvalidValue;
+    switch (id) {
+        case KernelId::P2GG2PBwd: k_p2g_g2p_bwd<<<a.n_chunks, kChunk, 0, s>>>(A, G); break;
+        case KernelId::P2GG2PBwdFp64: k_p2g_g2p_bwd_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(A, G); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -7,13 +7,18 @@
 namespace mpm {
 
 enum class KernelId : int {
-    P2G = 0, Grid, G2P, G2PBwd, GridBwd, P2GBwd, GridClear, SlotClear, P2GFp64, P2GBwdFp64, Count
+    P2G = 0, Grid, G2P, G2PBwd, GridBwd, P2GBwd, GridClear, SlotClear, P2GFp64, P2GBwdFp64, P2GG2PBwd,
+    P2GG2PBwdFp64, Count
 };
 constexpr int kFp64Ctas = 152;   // CTAs of the FP64 fix-up kernels (grid-stride over the deferred list)
 constexpr int kFp64Threads = 128;
 
 // one substep kernel; forward kernels read only A.f
 cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s);
+// the fused adjoint (P2GG2PBwd, P2GG2PBwdFp64): the P2G adjoint of substep k
+// (A) with the G2P adjoint of substep k-1 (G, whose gacc is the other grid
+// adjoint buffer); not with the regularisers or the scatter tile
+cudaError_t launch_fused(KernelId id, const AdjArgs& A, const AdjArgs& G, cudaStream_t s);
 cudaError_t launch_state_from_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* x,
                                   const float* v, const float* C, const float* F, float* s, cudaStream_t st);
 // statistics of the x, v, F adjoints of a state for the regularisers of

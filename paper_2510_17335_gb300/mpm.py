@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmpm_gb300.so")
 
 MPM_OK = 0
-PROFILE_KERNELS = 10    # MPM_PROFILE_KERNELS of the header
+PROFILE_KERNELS = 12    # MPM_PROFILE_KERNELS of the header
 ERRORS = {
     -1: "MPM_ERR_INVALID_ARG", -2: "MPM_ERR_OOM", -3: "MPM_ERR_CUDA", -4: "MPM_ERR_OUT_OF_DOMAIN",
     -5: "MPM_ERR_NON_FINITE", -6: "MPM_ERR_NO_RECORD", -7: "MPM_ERR_TIMEOUT", -8: "MPM_ERR_NO_DEVICE",
@@ -50,7 +50,7 @@ class mpm_options(ctypes.Structure):
     _fields_ = [("checkpoint_every", ctypes.c_int), ("clip_grads", ctypes.c_int), ("clip_value", ctypes.c_double),
                 ("sigma_min", ctypes.c_double), ("sort_every", ctypes.c_int), ("tile_scatter", ctypes.c_int),
                 ("cuda_graphs", ctypes.c_int), ("grad_scale", ctypes.c_int), ("oom_star", ctypes.c_double),
-                ("grad_delta", ctypes.c_double)]
+                ("grad_delta", ctypes.c_double), ("fuse_adjoint", ctypes.c_int)]
 
 
 class mpm_skill(ctypes.Structure):
@@ -201,12 +201,14 @@ def make_skill(theta, v_lin, v_ang, substeps_per_action, start_pose, unrounded_T
 
 
 def make_options(checkpoint_every=50, clip_grads=0, clip_value=1e4, sigma_min=1e-4, sort_every=0,
-                 tile_scatter=0, cuda_graphs=1, grad_scale=0, oom_star=4.0, grad_delta=1e-6) -> mpm_options:
+                 tile_scatter=0, cuda_graphs=1, grad_scale=0, oom_star=4.0, grad_delta=1e-6,
+                 fuse_adjoint=1) -> mpm_options:
     o = mpm_options()
     o.checkpoint_every, o.clip_grads, o.clip_value = int(checkpoint_every), int(clip_grads), float(clip_value)
     o.sigma_min, o.sort_every, o.tile_scatter = float(sigma_min), int(sort_every), int(tile_scatter)
     o.cuda_graphs = int(cuda_graphs)
     o.grad_scale, o.oom_star, o.grad_delta = int(grad_scale), float(oom_star), float(grad_delta)
+    o.fuse_adjoint = int(fuse_adjoint)
     return o
 
 
