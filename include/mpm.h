@@ -208,6 +208,20 @@ int mpm_height_map(mpm_handle* h, const mpm_obs_grid* grids, float* maps, int de
 int mpm_loss_hmd(mpm_handle* h, const mpm_obs_grid* grids, const float* target_maps, double* loss, float* dL_dx,
                  int device_ptrs);
 
+/* The unnormalised Earth Mover's distance of Eq. (1) per instance between
+ * the observation of mpm_surface_observation (grids; its non-empty pixels)
+ * and a target cloud: loss[i] = min over one-to-one maps phi of
+ * sum |x - phi(x)| (FP64, host). targets: n_inst * res^2 * 3 floats, the
+ * first n_targets[i] rows (host ints) of instance i are its points; the map
+ * needs n_targets[i] >= the observed points (else MPM_ERR_INVALID_ARG).
+ * Found by an auction with epsilon scaling (Bertsekas); the result is within
+ * (observed points) * 1e-6 * size of the optimum. dL_dx (may be NULL):
+ * n_particles * 3, (x - phi(x)) / |x - phi(x)| on each observed particle,
+ * 0 elsewhere. MPM_ERR_TIMEOUT if the auction does not finish within its
+ * round limit. */
+int mpm_loss_emd(mpm_handle* h, const mpm_obs_grid* grids, const float* targets, const int* n_targets,
+                 double* loss, float* dL_dx, int device_ptrs);
+
 /* The line search of Sec. III-F, batched: instances 0..n_cand-1 of h are the
  * candidates (the caller has set their start state); each gets mats[k]
  * and/or skills[k] (either may be NULL), all advance n_substeps in one

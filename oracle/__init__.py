@@ -8,8 +8,9 @@ which holds none of the method's arithmetic.
 
 The arithmetic lives in ``oracle.c`` (plain C, FP64, compiled with
 ``-ffp-contract=off`` so that x86 and Arm give the same bits). This module is
-argument marshalling plus two textbook definitions written in numpy (the MSE
-loss of a final position set and its gradient).
+argument marshalling plus textbook definitions written in numpy: the MSE loss
+of a final position set and its gradient, and the unnormalised Earth Mover's
+distance of Eq. (1) with scipy's linear assignment as its one library step.
 """
 from __future__ import annotations
 
@@ -361,3 +362,23 @@ def grad_op(p: Params, g) -> np.ndarray:
     pc = p.c()
     _L().orc_grad_op(ctypes.byref(pc), _d(g), g.size)
     return g
+
+
+def emd(X, Xhat) -> tuple[float, np.ndarray, np.ndarray]:
+    """Unnormalised Earth Mover's distance of Eq. (1) (Sec. III-A, "Goal and
+    reward/loss"): the least total Euclidean distance over one-to-one maps
+    phi of the points X into Xhat (|X| <= |Xhat|), found by linear
+    assignment. Returns (d_EMD, phi as indices into Xhat, dd/dX): with phi
+    fixed, dd/dx = (x - phi(x)) / |x - phi(x)| (0 where they coincide)."""
+    from scipy.optimize import linear_sum_assignment
+    X = np.asarray(X, np.float64).reshape(-1, 3)
+    Y = np.asarray(Xhat, np.float64).reshape(-1, 3)
+    assert X.shape[0] <= Y.shape[0]
+    D = np.sqrt(((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
+    rows, cols = linear_sum_assignment(D)
+    phi = np.empty(X.shape[0], np.int64)
+    phi[rows] = cols
+    diff = X - Y[phi]
+    dist = np.sqrt((diff * diff).sum(1))
+    grad = np.where(dist[:, None] > 0, diff / np.where(dist > 0, dist, 1.0)[:, None], 0.0)
+    return float(dist.sum()), phi, grad

@@ -155,6 +155,10 @@ struct mpm_handle {
     DevBuf<float> d_obs_out, d_obs_target;
     DevBuf<double> d_obs_loss;
     DevBuf<int> d_obs_count;
+    // Earth Mover's distance (auction)
+    DevBuf<float> d_emd_price;
+    DevBuf<int> d_emd_owner, d_emd_assign, d_emd_ntg, d_emd_cnt;
+    DevBuf<unsigned long long> d_emd_bids;
 
     // record / backward
     int64_t substep = 0;
@@ -522,6 +526,7 @@ int run_fused(mpm_handle* h, KernelId id, const AdjArgs& A, const AdjArgs& G) {
     return MPM_OK;
 }
 
+
 int run_substep(mpm_handle* h, const StepArgs& a) {
     AdjArgs A;
     std::memset(&A, 0, sizeof A);
@@ -572,18 +577,23 @@ StepArgs slot_args(mpm_handle* h, int k, int64_t substep) {
     return a;
 }
 
-// run one recorded substep into slot k (clearing the slot's old accumulators first)
-int run_slot_substep(mpm_handle* h, int k, int64_t substep) {
-    RK(ensure_slot(h, k));
-    StepArgs a = slot_args(h, k, substep);
-    if (h->seg_dirty[k]) {
-        AdjArgs C;
-        std::memset(&C, 0, sizeof C);
-        C.f = a;
-        RK(run_kernel(h, KernelId::SlotClear, C));
+
+// Recorded substeps k0 .. k0+cnt-1 of the current segment (global substep
+// s0 for k0), each into its slot (cleared first if it holds old sums).
+int run_slot_range(mpm_handle* h, int k0, int cnt, int64_t s0) {
+    for (int t = 0; t < cnt; t++) {
+        const int k = k0 + t;
+        RK(ensure_slot(h, k));
+        const StepArgs a = slot_args(h, k, s0 + t);
+        if (h->seg_dirty[k]) {
+            AdjArgs C;
+            std::memset(&C, 0, sizeof C);
+            C.f = a;
+            RK(run_kernel(h, KernelId::SlotClear, C));
+        }
+        h->seg_dirty[k] = 1;
+        RK(run_substep(h, a));
     }
-    RK(run_substep(h, a));
-    h->seg_dirty[k] = 1;
     return MPM_OK;
 }
 
@@ -781,6 +791,8 @@ void mpm_destroy(mpm_handle* h) {
     h->d_loss.release(); h->d_fb_list.release(); h->d_fb_count.release();
     h->d_obs.release(); h->d_keys.release(); h->d_obs_out.release(); h->d_obs_target.release();
     h->d_obs_loss.release(); h->d_obs_count.release();
+    h->d_emd_price.release(); h->d_emd_owner.release(); h->d_emd_assign.release(); h->d_emd_ntg.release();
+    h->d_emd_cnt.release(); h->d_emd_bids.release();
     for (auto& c : h->ckpt) c.release();
     for (auto& b : h->seg_state) b.release();
     for (auto& b : h->seg_acc) b.release();
@@ -1105,7 +1117,7 @@ static int forward_launch(mpm_handle* h, int n_substeps, int record) {
         // last segment without recomputing it. Earlier segments are
         // recomputed from their checkpoints.
         const float* cur = h->d_state.p;
-        for (int i = 0; i < n_substeps; i++) {
+        for (int i = 0; i < n_substeps;) {
             const int64_t j = h->rec_len / K;
             const int k = (int)(h->rec_len % K);
             if (k == 0) {
@@ -1136,11 +1148,14 @@ static int forward_launch(mpm_handle* h, int n_substeps, int record) {
                 h->seg_valid = j;
                 h->seg_valid_len = 0;
             }
-            RK(run_slot_substep(h, k, h->substep));
-            cur = h->seg_state[k + 1].p;
-            h->seg_valid_len = k + 1;
-            h->substep++;
-            h->rec_len++;
+            // the rest of this call within the segment
+            const int cnt = (int)std::min<int64_t>(K - k, n_substeps - i);
+            RK(run_slot_range(h, k, cnt, h->substep));
+            cur = h->seg_state[k + cnt].p;
+            h->seg_valid_len = k + cnt;
+            h->substep += cnt;
+            h->rec_len += cnt;
+            i += cnt;
         }
         RK(copy_state(h, h->d_state.p, cur));
     }
@@ -1184,7 +1199,7 @@ static int backward_launch(mpm_handle* h, const float* gx, const float* gv, bool
             // recompute the segment from its checkpoint, keeping every state and grid
             RK(ensure_slot(h, 0));
             RK(copy_state(h, h->seg_state[0].p, h->ckpt[j].p));
-            for (int i = 0; i < seg_len; i++) RK(run_slot_substep(h, i, h->rec_start + seg_begin + i));
+            RK(run_slot_range(h, 0, seg_len, h->rec_start + seg_begin));
             h->seg_valid = j;
             h->seg_valid_len = seg_len;
         }
@@ -1679,6 +1694,88 @@ int mpm_loss_hmd(mpm_handle* h, const mpm_obs_grid* grids, const float* target_m
     h->launches++;
     CK(cudaMemcpyAsync(loss, h->d_obs_loss.p, (size_t)n_inst * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (dL_dx && !device_ptrs && n) CK(cudaMemcpyAsync(dL_dx, g, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MPM_OK;
+}
+
+int mpm_loss_emd(mpm_handle* h, const mpm_obs_grid* grids, const float* targets, const int* n_targets,
+                 double* loss, float* dL_dx, int device_ptrs) {
+    if (!h || !targets || !n_targets || !loss) return MPM_ERR_INVALID_ARG;
+    int npix = 0;
+    RK(obs_keys(h, grids, 0, &npix));
+    const int n_inst = (int)h->inst.size();
+    const int n = n_inst * npix;
+    const size_t n_ext = (size_t)h->n_ext;
+    cudaStream_t s = h->stream;
+    // the observed points (NaN where a pixel is empty) and their counts
+    RK(h->d_obs_out.ensure((size_t)n * 3, h->device_bytes));
+    RK(h->d_obs_count.ensure((size_t)n_inst, h->device_bytes));
+    CK(cudaMemsetAsync(h->d_obs_out.p, 0xff, (size_t)n * 3 * sizeof(float), s));
+    CK(launch_obs_points(h->d_inst.p, h->d_chunk_inst.p, h->n_chunks, h->ncap, h->d_ext_of_slot.p, h->d_state.p,
+                         h->d_obs.p, npix, h->d_keys.p, h->d_obs_out.p, s));
+    CK(launch_obs_maps(h->d_inst.p, n_inst, npix, h->d_keys.p, nullptr, nullptr, nullptr, nullptr,
+                       h->d_obs_count.p, s));
+    h->launches += 2;
+    std::vector<int> cnt(n_inst);
+    CK(cudaMemcpyAsync(cnt.data(), h->d_obs_count.p, n_inst * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // a one-to-one map needs at least as many targets as observed points
+    for (int i = 0; i < n_inst; i++)
+        if (n_targets[i] < cnt[i] || n_targets[i] > npix) return MPM_ERR_INVALID_ARG;
+    // targets, zero prices, the auction's arrays
+    RK(h->d_obs_target.ensure((size_t)n * 3, h->device_bytes));
+    RK(h->d_emd_price.ensure((size_t)n, h->device_bytes));
+    RK(h->d_emd_owner.ensure((size_t)n, h->device_bytes));
+    RK(h->d_emd_assign.ensure((size_t)n, h->device_bytes));
+    RK(h->d_emd_bids.ensure((size_t)n, h->device_bytes));
+    RK(h->d_emd_ntg.ensure((size_t)n_inst, h->device_bytes));
+    RK(h->d_emd_cnt.ensure(1, h->device_bytes));
+    RK(h->d_obs_loss.ensure((size_t)n_inst, h->device_bytes));
+    CK(cudaMemcpyAsync(h->d_obs_target.p, targets, (size_t)n * 3 * sizeof(float),
+                       device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->d_emd_ntg.p, n_targets, n_inst * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(h->d_emd_price.p, 0, (size_t)n * sizeof(float), s));
+    CK(cudaMemsetAsync(h->d_emd_bids.p, 0, (size_t)n * sizeof(unsigned long long), s));
+    // epsilon scaling: from a quarter of the largest square side down to 1e-6
+    // of it (a bid must stay several FP32 ulps above prices of that order)
+    double side = 0.0;
+    for (int i = 0; i < n_inst; i++) side = std::max(side, grids[i].size);
+    const double eps_final = 1e-6 * side;
+    constexpr int kRoundsPerCheck = 8;
+    constexpr int64_t kMaxRounds = 2000000;   // per phase: an unfinished auction is an error, not a hang
+    for (double eps = 0.25 * side;; eps = std::max(eps / 5.0, eps_final)) {
+        CK(launch_emd_reset(n, h->d_emd_owner.p, h->d_emd_assign.p, s));
+        h->launches++;
+        int64_t rounds = 0;
+        for (;;) {
+            int bidders = 0;
+            for (int r = 0; r < kRoundsPerCheck; r++) {
+                CK(cudaMemsetAsync(h->d_emd_cnt.p, 0, sizeof(int), s));
+                CK(launch_emd_round(n_inst, npix, h->d_obs_out.p, h->d_obs_target.p, h->d_emd_ntg.p,
+                                    h->d_emd_owner.p, h->d_emd_assign.p, h->d_emd_price.p, h->d_emd_bids.p,
+                                    (float)eps, h->d_emd_cnt.p, s));
+                h->launches += 2;
+            }
+            rounds += kRoundsPerCheck;
+            CK(cudaMemcpyAsync(&bidders, h->d_emd_cnt.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (bidders == 0) break;
+            if (rounds >= kMaxRounds) return MPM_ERR_TIMEOUT;
+        }
+        if (eps <= eps_final) break;
+    }
+    // the distance and its gradient w.r.t. the observed particles
+    float* g = dL_dx;
+    if (dL_dx && !device_ptrs) {
+        RK(ensure_stage(h));
+        g = h->d_stage.p;
+    }
+    if (g && n_ext) CK(cudaMemsetAsync(g, 0, n_ext * 3 * sizeof(float), s));
+    CK(launch_emd_loss(h->d_inst.p, n_inst, npix, h->d_obs_out.p, h->d_obs_target.p, h->d_emd_assign.p,
+                       h->d_keys.p, h->d_obs_loss.p, g, s));
+    h->launches++;
+    CK(cudaMemcpyAsync(loss, h->d_obs_loss.p, n_inst * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (dL_dx && !device_ptrs && n_ext) CK(cudaMemcpyAsync(dL_dx, g, n_ext * 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return MPM_OK;
 }

@@ -398,29 +398,24 @@ __device__ __forceinline__ void g2p_gather(const Stencil& st, const Nodes& src, 
     }
 }
 
-__global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
-    __shared__ InstDev sI;
-    const int inst = a.chunk_inst[blockIdx.x];
-    const InstDev& I = stage_instance(sI, a.inst, inst);
-    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
-    if (p - I.pbeg >= I.n) return;
+// G2P of one particle (Algorithm 1: gather of v and C, particle contact,
+// advection) into x, v, C of a.sout; returns them in xn, v, C as well.
+__device__ __forceinline__ void g2p_particle(const InstDev& I, const StepArgs& a, long long p, float (&xn)[3],
+                                             float (&v)[3], float (&C)[3][3]) {
     const long long N = a.ncap;
     float x[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) x[k] = ld(a.sin, N, kX + k, p);
     Stencil st;
     make_stencil(I, x, st);
-    float v[3], B[3][3];
+    float B[3][3];
     g2p_gather(st, GlobalNodes(I, st, a.vout), v, B);
-    // C = 4/dx^2 sum W v d^T with d = (o - f) dx
-    const float cscale = 4.0f * I.inv_dx;
     if (I.pcoll && I.shovel_on) {
         const Pose P = load_pose(I, a.substep);
         float sn, cs;
         sincosf(P.psi, &sn, &cs);
         shovel_project(I, P, cs, sn, x, v);
     }
-    float xn[3];
     bool finite = true;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -435,6 +430,8 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
     }
     if (!finite) atomicOr(a.status, kStatusNonFinite);
     if (!inside) atomicOr(a.status, kStatusDomain);
+    // C = 4/dx^2 sum W v d^T with d = (o - f) dx
+    const float cscale = 4.0f * I.inv_dx;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         a.sout[(kX + k) * N + p] = xn[k];
@@ -443,8 +440,22 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
 #pragma unroll
     for (int r = 0; r < 3; r++)
 #pragma unroll
-        for (int c = 0; c < 3; c++) a.sout[(kC + 3 * r + c) * N + p] = cscale * B[r][c];
+        for (int c = 0; c < 3; c++) {
+            C[r][c] = cscale * B[r][c];
+            a.sout[(kC + 3 * r + c) * N + p] = C[r][c];
+        }
 }
+
+__global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
+    __shared__ InstDev sI;
+    const int inst = a.chunk_inst[blockIdx.x];
+    const InstDev& I = stage_instance(sI, a.inst, inst);
+    const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (p - I.pbeg >= I.n) return;
+    float xn[3], v[3], C[3][3];
+    g2p_particle(I, a, p, xn, v, C);
+}
+
 
 // ---------------------------------------------------------------------------
 // adjoint

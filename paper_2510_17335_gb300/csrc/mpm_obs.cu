@@ -153,3 +153,150 @@ cudaError_t launch_obs_maps(const InstDev* inst, int n_inst, int npix, const uns
 }
 
 }  // namespace mpm
+
+// ---------------------------------------------------------------------------
+// Earth Mover's distance of Eq. (1) (Sec. III-A): the least total Euclidean
+// distance over one-to-one maps of an instance's observed points (the
+// non-empty pixels of its observation) into its target points, by an
+// auction (Bertsekas) with epsilon scaling. Bidders are pixels, objects are
+// target rows; a bidder's value of object j is -|x - y_j| - price_j. One
+// warp per unassigned bidder finds its best and second-best objects and bids
+// price + (best - second) + eps with a 64-bit atomicMax on (ordered bid,
+// bidder): the highest bid wins (ties: the higher bidder index), in any
+// launch order. Each phase ends with every bidder assigned; the final
+// assignment costs at most n * eps more than the optimum.
+// ---------------------------------------------------------------------------
+namespace mpm {
+namespace {
+
+__global__ void __launch_bounds__(256) k_emd_bid(int npix, const float* points, const float* targets,
+                                                 const int* n_targets, const int* assign, const float* price,
+                                                 unsigned long long* bids, float eps, int n_bidders,
+                                                 int* unassigned) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= n_bidders) return;
+    const float* xp = points + 3 * (long long)b;
+    const float x0 = xp[0], x1 = xp[1], x2 = xp[2];
+    if (x0 != x0 || assign[b] >= 0) return;   // empty pixel (NaN) or assigned
+    const int inst = b / npix;
+    const int m = n_targets[inst];
+    const float* tg = targets + 3 * (long long)inst * npix;
+    const float* pr = price + (long long)inst * npix;
+    float v1 = -3.0e38f, v2 = -3.0e38f;
+    int j1 = -1;
+    for (int j = lane; j < m; j += 32) {
+        const float d0 = x0 - tg[3 * j], d1 = x1 - tg[3 * j + 1], d2 = x2 - tg[3 * j + 2];
+        const float v = -sqrtf(d0 * d0 + d1 * d1 + d2 * d2) - pr[j];
+        if (v > v1) { v2 = v1; v1 = v; j1 = j; }
+        else if (v > v2) v2 = v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov1 = __shfl_xor_sync(0xffffffffu, v1, o), ov2 = __shfl_xor_sync(0xffffffffu, v2, o);
+        const int oj1 = __shfl_xor_sync(0xffffffffu, j1, o);
+        // merge the two (best, second) pairs; equal values: the lower object
+        const bool take = ov1 > v1 || (ov1 == v1 && oj1 >= 0 && (j1 < 0 || oj1 < j1));
+        const float nv2 = take ? fmaxf(v1, ov2) : fmaxf(v2, ov1);
+        if (take) { v1 = ov1; j1 = oj1; }
+        v2 = nv2;
+    }
+    if (lane == 0 && j1 >= 0) {
+        // with a single object the second best is minus infinity: bid its price + eps
+        const float inc = (v2 > -3.0e38f ? v1 - v2 : 0.0f) + eps;
+        const float bid = pr[j1] + inc;
+        const unsigned u = __float_as_uint(bid);
+        const unsigned ob = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+        atomicMax(bids + (long long)inst * npix + j1, ((unsigned long long)ob << 32) | (unsigned)b);
+        atomicAdd(unassigned, 1);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_emd_resolve(int n_objects, int* owner, int* assign, float* price,
+                                                     unsigned long long* bids) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_objects) return;
+    const unsigned long long k = bids[j];
+    if (k == 0ull) return;
+    bids[j] = 0ull;
+    const int winner = (int)(k & 0xffffffffull);
+    const unsigned ob = (unsigned)(k >> 32);
+    price[j] = __uint_as_float((ob & 0x80000000u) ? (ob & 0x7fffffffu) : ~ob);
+    const int prev = owner[j];
+    // only unassigned bidders bid, so the previous owner did not win elsewhere this round
+    if (prev >= 0) assign[prev] = -1;
+    owner[j] = winner;
+    assign[winner] = j;   // flat object index: instance * npix + target row
+}
+
+// a new phase: nobody assigned, prices kept
+__global__ void __launch_bounds__(256) k_emd_reset(int n, int* owner, int* assign) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        owner[j] = -1;
+        assign[j] = -1;
+    }
+}
+
+// one CTA per instance: d_EMD (FP64, fixed order) and the gradient of each
+// observed particle, (x - y) / |x - y|, into dL_dx (external order) through
+// the observation's winner keys
+__global__ void __launch_bounds__(256) k_emd_loss(const InstDev* inst, int npix, const float* points,
+                                                  const float* targets, const int* assign,
+                                                  const unsigned long long* keys, double* loss, float* dL_dx) {
+    const int i = blockIdx.x;
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < npix; q += blockDim.x) {
+        const long long b = (long long)i * npix + q;
+        const int a = assign[b];
+        if (a < 0) continue;
+        const float* x = points + 3 * b;
+        const float* y = targets + 3 * (long long)a;
+        const float d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+        const double dist = sqrt((double)d0 * d0 + (double)d1 * d1 + (double)d2 * d2);
+        acc += dist;
+        if (dL_dx && dist > 0.0) {
+            const long long e = inst[i].ext_off + (long long)(0xffffffffu - (unsigned)(keys[b] & 0xffffffffull));
+            dL_dx[3 * e + 0] = (float)(d0 / dist);
+            dL_dx[3 * e + 1] = (float)(d1 / dist);
+            dL_dx[3 * e + 2] = (float)(d2 / dist);
+        }
+    }
+    __shared__ double sacc[256];
+    sacc[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sacc[threadIdx.x] += sacc[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss[i] = sacc[0];
+}
+
+}  // namespace
+
+cudaError_t launch_emd_reset(int n, int* owner, int* assign, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_emd_reset<<<(n + 255) / 256, 256, 0, st>>>(n, owner, assign);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emd_round(int n_inst, int npix, const float* points, const float* targets, const int* n_targets,
+                             int* owner, int* assign, float* price, unsigned long long* bids, float eps,
+                             int* unassigned, cudaStream_t st) {
+    const int n = n_inst * npix;
+    if (n <= 0) return cudaSuccess;
+    k_emd_bid<<<(n * 32 + 255) / 256, 256, 0, st>>>(npix, points, targets, n_targets, assign, price, bids, eps, n,
+                                                    unassigned);
+    k_emd_resolve<<<(n + 255) / 256, 256, 0, st>>>(n, owner, assign, price, bids);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emd_loss(const InstDev* inst, int n_inst, int npix, const float* points, const float* targets,
+                            const int* assign, const unsigned long long* keys, double* loss, float* dL_dx,
+                            cudaStream_t st) {
+    if (n_inst <= 0) return cudaSuccess;
+    k_emd_loss<<<n_inst, 256, 0, st>>>(inst, npix, points, targets, assign, keys, loss, dL_dx);
+    return cudaGetLastError();
+}
+
+}  // namespace mpm

@@ -111,6 +111,7 @@ EXPORTS = {
     "mpm_surface_observation": (_ip, [_vp, ctypes.POINTER(mpm_obs_grid), _fp, ctypes.POINTER(ctypes.c_int), _ip]),
     "mpm_height_map": (_ip, [_vp, ctypes.POINTER(mpm_obs_grid), _fp, _ip]),
     "mpm_loss_hmd": (_ip, [_vp, ctypes.POINTER(mpm_obs_grid), _fp, _dp, _fp, _ip]),
+    "mpm_loss_emd": (_ip, [_vp, ctypes.POINTER(mpm_obs_grid), _fp, ctypes.POINTER(ctypes.c_int), _dp, _fp, _ip]),
     "mpm_line_search": (_ip, [_vp, _ip, ctypes.POINTER(mpm_material), ctypes.POINTER(mpm_skill), _ip,
                               ctypes.POINTER(mpm_obs_grid), _fp, _ip, _dp, ctypes.POINTER(ctypes.c_int)]),
     "mpm_destroy": (None, [_vp]),
@@ -396,6 +397,25 @@ class Simulation:
         g = np.empty((self.n, 3), np.float32) if want_grad else None
         check(lib().mpm_loss_hmd(self.h, ga, tm.ctypes.data_as(ctypes.c_void_p), L.ctypes.data_as(_dp),
                                  g.ctypes.data_as(ctypes.c_void_p) if g is not None else None, 0), "mpm_loss_hmd")
+        return L, g
+
+    def loss_emd(self, grids, targets, want_grad: bool = True):
+        """Earth Mover's distance of the observation to target clouds (Eq. (1)):
+        targets is a list of [m_i, 3] arrays (m_i <= res^2). Returns (loss [n_inst]
+        (FP64), dL/dx [n, 3] or None)."""
+        ga = self._grids(grids)
+        npix = ga[0].res * ga[0].res
+        tg = np.full((self.n_inst, npix, 3), np.nan, np.float32)
+        nt = (ctypes.c_int * self.n_inst)()
+        for i, t in enumerate(targets):
+            t = np.asarray(t, np.float32).reshape(-1, 3)
+            assert t.shape[0] <= npix
+            tg[i, :t.shape[0]] = t
+            nt[i] = t.shape[0]
+        L = np.zeros(self.n_inst, np.float64)
+        g = np.empty((self.n, 3), np.float32) if want_grad else None
+        check(lib().mpm_loss_emd(self.h, ga, tg.ctypes.data_as(ctypes.c_void_p), nt, L.ctypes.data_as(_dp),
+                                 g.ctypes.data_as(ctypes.c_void_p) if g is not None else None, 0), "mpm_loss_emd")
         return L, g
 
     def line_search(self, n_substeps: int, grids, target_maps, materials=None, skills=None):

@@ -149,3 +149,43 @@ def test_batched_line_search_matches_oracle():
     assert best == int(np.argmin(Lo)) == 2
     # FP32 and FP64 trajectories give heights a few 1e-7 apart per pixel
     assert np.allclose(L, Lo, rtol=0.02, atol=1e-3)
+
+
+@pytest.mark.parametrize("n_extra", [0, 37])
+def test_emd_matches_oracle(n_extra):
+    """Earth Mover's distance of Eq. (1) between the observation and a target
+    cloud: the GPU auction's distance lies between the optimum (oracle, by
+    linear assignment on the same FP32 points) and the optimum plus
+    n * eps_final; its gradient is a unit vector on every observed particle
+    and zero elsewhere, and equals the oracle's where the maps agree."""
+    w = W.cfg_small()
+    c = _bed_centre(w)
+    size = 0.24
+    g = mpm.make_obs_grid(c, size, 40, 0.0)
+    g_o = oracle.ObsGrid(c[0], c[1], size, 40, 0.0)
+    rng = np.random.default_rng(40 + n_extra)
+    with mpm.simulation_from_workloads([w]) as sim:
+        sim.forward(150)
+        x = sim.get_state()["x"]
+        pts, cnt = sim.surface_observation(g)
+        X = pts[0][~np.isnan(pts[0][:, 0])]
+        tgt = (X + np.array([0.004, -0.006, 0.002], np.float32)
+               + 0.003 * rng.normal(size=X.shape).astype(np.float32)).astype(np.float32)
+        if n_extra:
+            tgt = np.concatenate([tgt, (X[:n_extra] + 0.02).astype(np.float32)])
+        tgt = tgt[rng.permutation(tgt.shape[0])]
+        L, grad = sim.loss_emd(g, [tgt])
+    n_obs, idx = oracle.surface_observation(g_o, x)
+    assert n_obs == X.shape[0] == cnt[0]
+    Lo, phi, go = oracle.emd(X, tgt)
+    eps_final = 1e-6 * size
+    print("EMD gpu", L[0], "oracle", Lo, "n eps", n_obs * eps_final)
+    assert Lo * (1 - 1e-6) <= L[0] <= Lo + n_obs * eps_final + 1e-6 * Lo
+    owners = idx[idx >= 0]                       # particle of each observed pixel, pixel order
+    norms = np.linalg.norm(grad[owners], axis=1)
+    assert np.allclose(norms, 1.0, atol=1e-5)
+    others = np.setdiff1d(np.arange(x.shape[0]), owners)
+    assert not grad[others].any()
+    same = np.all(np.abs(grad[owners] - go.astype(np.float32)) < 1e-4, axis=1)
+    print("gradient rows equal to the oracle's:", same.mean())
+    assert same.mean() > 0.9
