@@ -31,11 +31,18 @@ sys.path.insert(0, ROOT)
 
 # algorithmic bytes per particle per launch (FP32 state; reads + writes the
 # method needs, grid traffic not counted)
+# Algorithmic bytes per particle and launch: what the method must read and
+# write (FP32 state); the recorded SVD a recorded forward writes and the
+# adjoint reads back (96 B) is a compute-saving choice and shows in the
+# measured DRAM traffic, not here.
 ALGO_BYTES = {
     "k_p2g": 96 + 36,          # read x, v, C, F; write F
     "k_g2p": 12 + 60,          # read x; write x, v, C
     "k_g2p_bwd": 12 + 60 + 12,  # read x, adj x/v/C; write adj x
     "k_p2g_bwd": 96 + 48 + 96,  # read state and adj x/F; write adj x/v/C/F
+    # fused P2G adjoint of substep k + G2P adjoint of k-1: read state k and
+    # adj x/F, write adj F and (partial) x, read x of state k-1
+    "k_p2g_g2p_bwd": 96 + 48 + 48 + 12,
 }
 
 

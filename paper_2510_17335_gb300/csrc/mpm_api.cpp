@@ -1704,6 +1704,7 @@ int mpm_loss_emd(mpm_handle* h, const mpm_obs_grid* grids, const float* targets,
     int npix = 0;
     RK(obs_keys(h, grids, 0, &npix));
     const int n_inst = (int)h->inst.size();
+    if (2LL * n_inst * npix >= 0x7fffffffLL) return MPM_ERR_INVALID_ARG;   // bidder indices are 32-bit
     const int n = n_inst * npix;
     const size_t n_ext = (size_t)h->n_ext;
     cudaStream_t s = h->stream;
@@ -1726,7 +1727,7 @@ int mpm_loss_emd(mpm_handle* h, const mpm_obs_grid* grids, const float* targets,
     RK(h->d_obs_target.ensure((size_t)n * 3, h->device_bytes));
     RK(h->d_emd_price.ensure((size_t)n, h->device_bytes));
     RK(h->d_emd_owner.ensure((size_t)n, h->device_bytes));
-    RK(h->d_emd_assign.ensure((size_t)n, h->device_bytes));
+    RK(h->d_emd_assign.ensure((size_t)2 * n, h->device_bytes));
     RK(h->d_emd_bids.ensure((size_t)n, h->device_bytes));
     RK(h->d_emd_ntg.ensure((size_t)n_inst, h->device_bytes));
     RK(h->d_emd_cnt.ensure(1, h->device_bytes));
@@ -1752,8 +1753,8 @@ int mpm_loss_emd(mpm_handle* h, const mpm_obs_grid* grids, const float* targets,
             for (int r = 0; r < kRoundsPerCheck; r++) {
                 CK(cudaMemsetAsync(h->d_emd_cnt.p, 0, sizeof(int), s));
                 CK(launch_emd_round(n_inst, npix, h->d_obs_out.p, h->d_obs_target.p, h->d_emd_ntg.p,
-                                    h->d_emd_owner.p, h->d_emd_assign.p, h->d_emd_price.p, h->d_emd_bids.p,
-                                    (float)eps, h->d_emd_cnt.p, s));
+                                    h->d_obs_count.p, h->d_emd_owner.p, h->d_emd_assign.p, h->d_emd_price.p,
+                                    h->d_emd_bids.p, (float)eps, h->d_emd_cnt.p, s));
                 h->launches += 2;
             }
             rounds += kRoundsPerCheck;

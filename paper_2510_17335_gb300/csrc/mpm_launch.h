@@ -60,14 +60,15 @@ cudaError_t launch_obs_maps(const InstDev* inst, int n_inst, int npix, const uns
                             const float* target, double* loss, float* dL_dx, int* counts, cudaStream_t st);
 
 // Earth Mover's distance (Eq. (1)) by an auction over all instances: bidders
-// are observation pixels (points, NaN = empty), objects the first
-// n_targets[i] target rows of instance i; assign / owner hold flat indices
-// instance * npix + row / pixel. A round is one bid and one resolve kernel;
+// are observation pixels (points, NaN = empty) and n_targets[i] - counts[i]
+// zero-cost dummies per instance (flat indices n + instance * npix + d),
+// objects the first n_targets[i] target rows of instance i; assign (2n) /
+// owner (n) hold flat indices. A round is one bid and one resolve kernel;
 // *unassigned counts the bidders that bid (zero: the phase is over).
 cudaError_t launch_emd_reset(int n, int* owner, int* assign, cudaStream_t st);
 cudaError_t launch_emd_round(int n_inst, int npix, const float* points, const float* targets, const int* n_targets,
-                             int* owner, int* assign, float* price, unsigned long long* bids, float eps,
-                             int* unassigned, cudaStream_t st);
+                             const int* counts, int* owner, int* assign, float* price, unsigned long long* bids,
+                             float eps, int* unassigned, cudaStream_t st);
 // the distance per instance (FP64) and the gradient of the observed particles
 cudaError_t launch_emd_loss(const InstDev* inst, int n_inst, int npix, const float* points, const float* targets,
                             const int* assign, const unsigned long long* keys, double* loss, float* dL_dx,

@@ -169,25 +169,41 @@ cudaError_t launch_obs_maps(const InstDev* inst, int n_inst, int npix, const uns
 namespace mpm {
 namespace {
 
+// Bidders 0 .. n-1 are the pixels of all instances; bidders n .. 2n-1 are
+// dummies, n_targets[i] - counts[i] of them per instance, that value every
+// target at distance 0: they square the problem (as many bidders as
+// targets), which the forward auction with epsilon scaling needs to end at
+// the optimum when there are more targets than observed points.
 __global__ void __launch_bounds__(256) k_emd_bid(int npix, const float* points, const float* targets,
-                                                 const int* n_targets, const int* assign, const float* price,
-                                                 unsigned long long* bids, float eps, int n_bidders,
+                                                 const int* n_targets, const int* counts, const int* assign,
+                                                 const float* price, unsigned long long* bids, float eps, int n,
                                                  int* unassigned) {
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (b >= n_bidders) return;
-    const float* xp = points + 3 * (long long)b;
-    const float x0 = xp[0], x1 = xp[1], x2 = xp[2];
-    if (x0 != x0 || assign[b] >= 0) return;   // empty pixel (NaN) or assigned
-    const int inst = b / npix;
+    if (b >= 2 * n) return;
+    const bool dummy = b >= n;
+    const int inst = (dummy ? b - n : b) / npix;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    if (dummy) {
+        if ((b - n) % npix >= n_targets[inst] - counts[inst]) return;   // not one of this instance's dummies
+    } else {
+        const float* xp = points + 3 * (long long)b;
+        x0 = xp[0]; x1 = xp[1]; x2 = xp[2];
+        if (x0 != x0) return;   // empty pixel (NaN)
+    }
+    if (assign[b] >= 0) return;
     const int m = n_targets[inst];
     const float* tg = targets + 3 * (long long)inst * npix;
     const float* pr = price + (long long)inst * npix;
     float v1 = -3.0e38f, v2 = -3.0e38f;
     int j1 = -1;
     for (int j = lane; j < m; j += 32) {
-        const float d0 = x0 - tg[3 * j], d1 = x1 - tg[3 * j + 1], d2 = x2 - tg[3 * j + 2];
-        const float v = -sqrtf(d0 * d0 + d1 * d1 + d2 * d2) - pr[j];
+        float dist = 0.0f;
+        if (!dummy) {
+            const float d0 = x0 - tg[3 * j], d1 = x1 - tg[3 * j + 1], d2 = x2 - tg[3 * j + 2];
+            dist = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+        }
+        const float v = -dist - pr[j];
         if (v > v1) { v2 = v1; v1 = v; j1 = j; }
         else if (v > v2) v2 = v;
     }
@@ -229,13 +245,11 @@ __global__ void __launch_bounds__(256) k_emd_resolve(int n_objects, int* owner, 
     assign[winner] = j;   // flat object index: instance * npix + target row
 }
 
-// a new phase: nobody assigned, prices kept
+// a new phase: nobody assigned (n objects, 2n bidders), prices kept
 __global__ void __launch_bounds__(256) k_emd_reset(int n, int* owner, int* assign) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) {
-        owner[j] = -1;
-        assign[j] = -1;
-    }
+    if (j < n) owner[j] = -1;
+    if (j < 2 * n) assign[j] = -1;
 }
 
 // one CTA per instance: d_EMD (FP64, fixed order) and the gradient of each
@@ -276,17 +290,17 @@ __global__ void __launch_bounds__(256) k_emd_loss(const InstDev* inst, int npix,
 
 cudaError_t launch_emd_reset(int n, int* owner, int* assign, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_emd_reset<<<(n + 255) / 256, 256, 0, st>>>(n, owner, assign);
+    k_emd_reset<<<(2 * n + 255) / 256, 256, 0, st>>>(n, owner, assign);
     return cudaGetLastError();
 }
 
 cudaError_t launch_emd_round(int n_inst, int npix, const float* points, const float* targets, const int* n_targets,
-                             int* owner, int* assign, float* price, unsigned long long* bids, float eps,
-                             int* unassigned, cudaStream_t st) {
+                             const int* counts, int* owner, int* assign, float* price, unsigned long long* bids,
+                             float eps, int* unassigned, cudaStream_t st) {
     const int n = n_inst * npix;
     if (n <= 0) return cudaSuccess;
-    k_emd_bid<<<(n * 32 + 255) / 256, 256, 0, st>>>(npix, points, targets, n_targets, assign, price, bids, eps, n,
-                                                    unassigned);
+    k_emd_bid<<<(2 * n * 32 + 255) / 256, 256, 0, st>>>(npix, points, targets, n_targets, counts, assign, price,
+                                                        bids, eps, n, unassigned);
     k_emd_resolve<<<(n + 255) / 256, 256, 0, st>>>(n, owner, assign, price, bids);
     return cudaGetLastError();
 }

@@ -50,10 +50,11 @@ def _close(a, b, ref_a, ref_b):
     """Each of (x, L, dL/dmaterial, dL/dF) of run a within 10x the spread of
     two eager runs (ref_a, ref_b) of run b, plus a floor: absolute for the
     positions, relative per entry for the loss and the material gradient
-    (its four entries span many decades; dL/dE of a small bed carries ~1e-3
-    relative summation-order noise), relative to the largest entry for
-    dL/dF."""
-    floors = (("abs", 1e-6), ("each", 1e-7), ("each", 5e-3), ("max", 1e-4))
+    (its four entries span many decades and carry up to ~1e-2 relative
+    summation-order noise on small beds: the gradient bar of the parity
+    tests), relative to the largest entry for dL/dF. A replay that ignored
+    new parameters is caught by the material-change test."""
+    floors = (("abs", 1e-6), ("each", 1e-7), ("each", 2e-2), ("max", 1e-4))
     for u, v, ru, rv, (kind, fl) in zip(a, b, ref_a, ref_b, floors):
         u, v, ru, rv = (np.asarray(t, np.float64) for t in (u, v, ru, rv))
         if kind == "each":
