@@ -208,7 +208,7 @@ def batched_vs_serial(n_inst: int, nsub: int, steps: int, sort_every: int):
     # the same checkpoint policy as the main leg, for the whole batch (each
     # instance alone then fits too): both arms use the same interval
     nodes = sum(int(np.prod([-(-r // 4) * 4 for r in w.res])) for w in ws)
-    K = auto_checkpoint(nsub, 96 * n_total, 32 * nodes + nodes // 64 + 96 * n_total,
+    K = auto_checkpoint(nsub, 96 * n_total, 32 * nodes + nodes // 8 + 96 * n_total,
                         torch.cuda.mem_get_info()[0])
     opts = mpm.make_options(checkpoint_every=K, sort_every=sort_every)
 
@@ -280,7 +280,7 @@ def run_ours(args):
     nodes = int(np.prod([-(-r // 4) * 4 for r in w.res]))
     # per recorded substep: a state (96 B/particle), the grids (acc + vout +
     # flags) and the SVD of the trial F (96 B/particle)
-    slot_state, slot_grid = 96 * N, 32 * nodes + nodes // 64 + 96 * N
+    slot_state, slot_grid = 96 * N, 32 * nodes + nodes // 8 + 96 * N
     K = args.checkpoint or auto_checkpoint(S, slot_state, slot_grid, torch.cuda.mem_get_info(local)[0])
     record_bytes = (K + 1) * slot_state + K * slot_grid
     stream = torch.cuda.Stream()

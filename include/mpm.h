@@ -265,8 +265,10 @@ int mpm_get_state_grad(mpm_handle* h, float* gx, float* gv, float* gC, float* gF
 int mpm_get_action_grad(mpm_handle* h, int inst, double* dL_dactions, double* dL_dstart);
 
 /* Diagnostic: total grid mass per instance (n_inst doubles) after the last
- * forward substep's P2G; by the partition of unity of the B-spline weights
- * (Sec. III-A, MLS-MPM transfer) it equals sum_p rho V_p up to rounding. */
+ * forward substep's P2G (summed in FP64 by its grid update; a backward's
+ * recomputation of substeps leaves it alone); by the partition of unity of
+ * the B-spline weights (Sec. III-A, MLS-MPM transfer) it equals
+ * sum_p rho V_p up to rounding. */
 int mpm_grid_mass(mpm_handle* h, double* mass);
 
 /* Autotuner: from the current state, time a recorded forward of

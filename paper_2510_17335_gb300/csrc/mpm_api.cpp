@@ -24,6 +24,12 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// touched-block set of one substep (the layout StepArgs::flags describes):
+// n_blocks flags, list length, ticket, n_blocks list entries; the flags and
+// the two counters start at zero, the list needs no initial value
+size_t flag_ints(int n_blocks) { return 2 * (size_t)n_blocks + 2; }
+size_t flag_bytes_zeroed(int n_blocks) { return ((size_t)n_blocks + 2) * sizeof(int); }
+
 struct Instance {
     mpm_config cfg;
     mpm_material mat;
@@ -144,7 +150,8 @@ struct mpm_handle {
     DevBuf<int> d_chunk_inst, d_block_inst, d_ext_of_slot;
     DevBuf<float> d_state, d_x0, d_stage, d_poses, d_target;
     DevBuf<float4> d_acc, d_vout;
-    DevBuf<unsigned char> d_flags;
+    DevBuf<int> d_flags;            // touched-block flags, list length, ticket, list (flag_ints)
+    DevBuf<double> d_mass;          // grid mass per instance: running sums, last update's totals
     DevBuf<int> d_status;
     DevBuf<unsigned long long> d_fp64;
     DevBuf<int> d_fb_list, d_fb_count;   // particles deferred to the FP64 kernels
@@ -169,7 +176,7 @@ struct mpm_handle {
     // grids of substep k in seg_acc/seg_vout/seg_flags[k] (k = 0..K-1)
     std::vector<DevBuf<float>> seg_state;
     std::vector<DevBuf<float4>> seg_acc, seg_vout;
-    std::vector<DevBuf<unsigned char>> seg_flags;
+    std::vector<DevBuf<int>> seg_flags;
     std::vector<DevBuf<float>> seg_spec;   // SVD of the trial F of substep k (k = 0..K-1)
     std::vector<char> seg_dirty;      // grid slot k holds accumulators/flags to clear
     int64_t seg_valid = -1;           // segment whose states/grids the slots hold
@@ -461,6 +468,8 @@ StepArgs base_args(mpm_handle* h) {
     a.ncap = h->ncap;
     a.n_chunks = h->n_chunks;
     a.n_blocks = h->n_blocks;
+    a.n_inst = (int)h->inst.size();
+    a.mass = h->d_mass.p;
     a.status = h->d_status.p;
     a.fp64_count = h->d_fp64.p;
     a.fb_list = h->d_fb_list.p;
@@ -554,10 +563,10 @@ int ensure_slot(mpm_handle* h, int k) {
     if (h->seg_acc[k].p == nullptr) {
         RK(h->seg_acc[k].ensure((size_t)h->n_nodes, h->device_bytes));
         RK(h->seg_vout[k].ensure((size_t)h->n_nodes, h->device_bytes));
-        RK(h->seg_flags[k].ensure((size_t)h->n_blocks, h->device_bytes));
+        RK(h->seg_flags[k].ensure(flag_ints(h->n_blocks), h->device_bytes));
         RK(h->seg_spec[k].ensure((size_t)h->ncap * kSpecComps, h->device_bytes));
         CK(cudaMemsetAsync(h->seg_acc[k].p, 0, (size_t)h->n_nodes * sizeof(float4), h->stream));
-        CK(cudaMemsetAsync(h->seg_flags[k].p, 0, (size_t)h->n_blocks, h->stream));
+        CK(cudaMemsetAsync(h->seg_flags[k].p, 0, flag_bytes_zeroed(h->n_blocks), h->stream));
         h->seg_dirty[k] = 0;
     }
     return MPM_OK;
@@ -579,12 +588,14 @@ StepArgs slot_args(mpm_handle* h, int k, int64_t substep) {
 
 
 // Recorded substeps k0 .. k0+cnt-1 of the current segment (global substep
-// s0 for k0), each into its slot (cleared first if it holds old sums).
-int run_slot_range(mpm_handle* h, int k0, int cnt, int64_t s0) {
+// s0 for k0), each into its slot (cleared first if it holds old sums); a
+// backward's recomputation leaves the grid-mass totals alone (recompute).
+int run_slot_range(mpm_handle* h, int k0, int cnt, int64_t s0, bool recompute) {
     for (int t = 0; t < cnt; t++) {
         const int k = k0 + t;
         RK(ensure_slot(h, k));
-        const StepArgs a = slot_args(h, k, s0 + t);
+        StepArgs a = slot_args(h, k, s0 + t);
+        if (recompute) a.mass = nullptr;
         if (h->seg_dirty[k]) {
             AdjArgs C;
             std::memset(&C, 0, sizeof C);
@@ -749,7 +760,8 @@ int mpm_create(int n_inst, const mpm_config* cfgs, const mpm_material* mats, con
         (rc = h->d_state.ensure((size_t)h->ncap * kStateComps, h->device_bytes)) ||
         (rc = h->d_x0.ensure((size_t)std::max<int64_t>(n_ext, 1) * 3, h->device_bytes)) ||
         (rc = h->d_acc.ensure(node, h->device_bytes)) || (rc = h->d_vout.ensure(node, h->device_bytes)) ||
-        (rc = h->d_flags.ensure(blk, h->device_bytes)) || (rc = h->d_status.ensure(1, h->device_bytes)) ||
+        (rc = h->d_flags.ensure(flag_ints(blk), h->device_bytes)) || (rc = h->d_status.ensure(1, h->device_bytes)) ||
+        (rc = h->d_mass.ensure((size_t)n_inst * 2, h->device_bytes)) ||
         (rc = h->d_fp64.ensure(1, h->device_bytes)) || (rc = h->d_loss.ensure(n_inst, h->device_bytes)) ||
         (rc = h->d_fb_list.ensure(std::max<int64_t>(h->ncap, 1), h->device_bytes)) ||
         (rc = h->d_fb_count.ensure(2, h->device_bytes)))
@@ -767,7 +779,8 @@ int mpm_create(int n_inst, const mpm_config* cfgs, const mpm_material* mats, con
         cudaMemcpyAsync(h->d_ext_of_slot.p, eos.data(), eos.size() * sizeof(int), cudaMemcpyHostToDevice, s) ||
         (n_ext > 0 && cudaMemcpyAsync(h->d_x0.p, x0, (size_t)n_ext * 3 * sizeof(float), cudaMemcpyHostToDevice, s)) ||
         cudaMemsetAsync(h->d_acc.p, 0, node * sizeof(float4), s) ||
-        cudaMemsetAsync(h->d_vout.p, 0, node * sizeof(float4), s) || cudaMemsetAsync(h->d_flags.p, 0, blk, s) ||
+        cudaMemsetAsync(h->d_vout.p, 0, node * sizeof(float4), s) || cudaMemsetAsync(h->d_flags.p, 0, flag_bytes_zeroed(blk), s) ||
+        cudaMemsetAsync(h->d_mass.p, 0, (size_t)n_inst * 2 * sizeof(double), s) ||
         cudaMemsetAsync(h->d_status.p, 0, sizeof(int), s) ||
         cudaMemsetAsync(h->d_fp64.p, 0, sizeof(unsigned long long), s) ||
         cudaMemsetAsync(h->d_fb_count.p, 0, 2 * sizeof(int), s) || cudaStreamSynchronize(s)) {
@@ -787,7 +800,7 @@ void mpm_destroy(mpm_handle* h) {
     drop_graphs(h);
     h->d_inst.release(); h->d_chunk_inst.release(); h->d_block_inst.release(); h->d_ext_of_slot.release();
     h->d_state.release(); h->d_x0.release(); h->d_stage.release(); h->d_poses.release(); h->d_target.release();
-    h->d_acc.release(); h->d_vout.release(); h->d_flags.release(); h->d_status.release(); h->d_fp64.release();
+    h->d_acc.release(); h->d_vout.release(); h->d_flags.release(); h->d_mass.release(); h->d_status.release(); h->d_fp64.release();
     h->d_loss.release(); h->d_fb_list.release(); h->d_fb_count.release();
     h->d_obs.release(); h->d_keys.release(); h->d_obs_out.release(); h->d_obs_target.release();
     h->d_obs_loss.release(); h->d_obs_count.release();
@@ -1150,7 +1163,7 @@ static int forward_launch(mpm_handle* h, int n_substeps, int record) {
             }
             // the rest of this call within the segment
             const int cnt = (int)std::min<int64_t>(K - k, n_substeps - i);
-            RK(run_slot_range(h, k, cnt, h->substep));
+            RK(run_slot_range(h, k, cnt, h->substep, false));
             cur = h->seg_state[k + cnt].p;
             h->seg_valid_len = k + cnt;
             h->substep += cnt;
@@ -1199,7 +1212,7 @@ static int backward_launch(mpm_handle* h, const float* gx, const float* gv, bool
             // recompute the segment from its checkpoint, keeping every state and grid
             RK(ensure_slot(h, 0));
             RK(copy_state(h, h->seg_state[0].p, h->ckpt[j].p));
-            RK(run_slot_range(h, 0, seg_len, h->rec_start + seg_begin));
+            RK(run_slot_range(h, 0, seg_len, h->rec_start + seg_begin, true));
             h->seg_valid = j;
             h->seg_valid_len = seg_len;
         }
@@ -1561,10 +1574,8 @@ const char* mpm_kernel_name(int kernel) {
 int mpm_grid_mass(mpm_handle* h, double* mass) {
     if (!h || !mass) return MPM_ERR_INVALID_ARG;
     RK(set_device(h));
-    CK(cudaMemsetAsync(h->d_loss.p, 0, h->inst.size() * sizeof(double), h->stream));
-    CK(launch_grid_mass(h->d_inst.p, h->d_block_inst.p, h->n_blocks, h->d_vout.p, h->d_loss.p, h->stream));
-    h->launches++;
-    CK(cudaMemcpyAsync(mass, h->d_loss.p, h->inst.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    const size_t n_inst = h->inst.size();
+    CK(cudaMemcpyAsync(mass, h->d_mass.p + n_inst, n_inst * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return MPM_OK;
 }

@@ -917,9 +917,21 @@ __device__ __forceinline__ void tile_add(TileSmem& T, float4* grid, int gofs, co
     }
 }
 
+// Touched grid blocks of one substep, kept in the int array `flags`:
+//   flags[b] (b < n_blocks)     1 once block b received a P2G contribution
+//   flags[n_blocks]             number of listed blocks
+//   flags[n_blocks + 1]         CTA ticket of the kernel that walks the list
+//   flags[n_blocks + 2 + i]     the i-th listed block, in no particular order
+// The grid kernels walk the list instead of testing every block's flag.
+__device__ __forceinline__ void mark_block(int* flags, int n_blocks, int b) {
+    // test first: the load mostly hits L1; the thread whose exchange sets the
+    // flag lists the block
+    if (flags[b] == 0 && atomicExch(flags + b, 1) == 0) flags[n_blocks + 2 + atomicAdd(flags + n_blocks, 1)] = b;
+}
+
 // flush a tile to the global grid (blocked layout of instance I); marks the
 // grid blocks that received mass when flags != nullptr
-__device__ __forceinline__ void tile_flush(TileSmem& T, const InstDev& I, float4* grid, unsigned char* flags,
+__device__ __forceinline__ void tile_flush(TileSmem& T, const InstDev& I, float4* grid, int* flags, int n_blocks,
                                            int nthreads) {
     __syncthreads();
     if (!T.tiled) return;
@@ -933,10 +945,7 @@ __device__ __forceinline__ void tile_flush(TileSmem& T, const InstDev& I, float4
         const int ix = T.lo[0] + t / (T.dim[1] * T.dim[2]);
         const int ofs = (ix >> 2) * sx + (ix & 3) * 16 + (iy >> 2) * sy + (iy & 3) * 4 + (iz >> 2) * 64 + (iz & 3);
         atomicAdd(grid + I.node_off + ofs, v);
-        if (flags) {
-            unsigned char* f = flags + I.blk_off + ((ix >> 2) * I.nb[1] + (iy >> 2)) * I.nb[2] + (iz >> 2);
-            if (*f == 0) *f = 1;
-        }
+        if (flags) mark_block(flags, n_blocks, I.blk_off + ((ix >> 2) * I.nb[1] + (iy >> 2)) * I.nb[2] + (iz >> 2));
     }
 }
 

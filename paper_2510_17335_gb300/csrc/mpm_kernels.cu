@@ -17,6 +17,8 @@
 // budget of the main particle kernels is set by the FP32 path.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "mpm_device.cuh"
 #include "mpm_launch.h"
 
@@ -84,17 +86,28 @@ __device__ __forceinline__ const InstDev& stage_instance(InstDev& sI, const Inst
 }
 
 // mark the (up to 8) grid blocks a stencil touches
-__device__ __forceinline__ void mark_blocks(const InstDev& I, const Stencil& st, unsigned char* flags) {
+__device__ __forceinline__ void mark_blocks(const InstDev& I, const Stencil& st, int* flags, int n_blocks) {
     const int b0x = st.base[0] >> 2, b1x = (st.base[0] + 2) >> 2;
     const int b0y = st.base[1] >> 2, b1y = (st.base[1] + 2) >> 2;
     const int b0z = st.base[2] >> 2, b1z = (st.base[2] + 2) >> 2;
     for (int bx = b0x; bx <= b1x; bx++)
         for (int by = b0y; by <= b1y; by++)
-            for (int bz = b0z; bz <= b1z; bz++) {
-                // test first: the load mostly hits L1, a store always goes to L2
-                unsigned char* f = flags + I.blk_off + (bx * I.nb[1] + by) * I.nb[2] + bz;
-                if (*f == 0) *f = 1;
-            }
+            for (int bz = b0z; bz <= b1z; bz++)
+                mark_block(flags, n_blocks, I.blk_off + (bx * I.nb[1] + by) * I.nb[2] + bz);
+}
+
+// End of a kernel that walks a block list: true in the last CTA to finish,
+// after every CTA has read the list length on entry (the ticket is in
+// flags[n_blocks + 1]; the caller zeroes it)
+__device__ __forceinline__ bool list_last_cta(int* flags, int n_blocks) {
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(flags + n_blocks + 1, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    return last != 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -241,10 +254,10 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_P2G) k_p2g(StepArgs a) {
             spectral_outputs<float, float>(S, Fn, tau);
             p2g_store_affine(I, a, p, Fn, tau, C, A);
             p2g_scatter(&T, I, a.acc, st, v, A);
-            if (!T.tiled) mark_blocks(I, st, a.flags);
+            if (!T.tiled) mark_blocks(I, st, a.flags, a.n_blocks);
         }
     }
-    tile_flush(T, I, a.acc, a.flags, kChunk);
+    tile_flush(T, I, a.acc, a.flags, a.n_blocks, kChunk);
 }
 
 // Deferred-list bookkeeping of the FP64 fix-up kernels: every CTA reads the
@@ -288,7 +301,7 @@ __global__ void __launch_bounds__(kFp64Threads) k_p2g_fp64(StepArgs a) {
         constitutive_fp64(Ft, I.mu, I.lam, I.beta, I.smin, Fn, tau);
         p2g_store_affine(I, a, p, Fn, tau, C, A);
         p2g_scatter(nullptr, I, a.acc, st, v, A);
-        mark_blocks(I, st, a.flags);
+        mark_blocks(I, st, a.flags, a.n_blocks);
         atomicAdd(a.fp64_count, 1ull);
     }
     fb_end(a.fb_count);
@@ -310,18 +323,17 @@ __device__ __forceinline__ void grid_node(const InstDev& I, const Pose& P, float
     }
 }
 
-__global__ void __launch_bounds__(256) k_grid(StepArgs a) {
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= a.n_blocks) return;
-    if (a.flags[gw] == 0) return;
-    const InstDev& I = a.inst[a.block_inst[gw]];
+// grid update of one touched block gw (one warp, two nodes a lane)
+__device__ __forceinline__ void grid_block(const StepArgs& a, int gw, int lane) {
+    const int inst = a.block_inst[gw];
+    const InstDev& I = a.inst[inst];
     const int lb = gw - I.blk_off;
     const int bz = lb % I.nb[2], by = (lb / I.nb[2]) % I.nb[1], bx = lb / (I.nb[1] * I.nb[2]);
     const Pose P = load_pose(I, a.substep);
     float sn, cs;
     sincosf(P.psi, &sn, &cs);
     const long long base = I.node_off + (long long)lb * 64;
+    double m = 0.0;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int nd = lane + 32 * h;
@@ -339,8 +351,35 @@ __global__ void __launch_bounds__(256) k_grid(StepArgs a) {
         }
         a.vout[base + nd] = out;
         if (!a.keep_grid) a.acc[base + nd] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        m += (double)acc.x;
+    }
+    if (a.mass) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
+        if (lane == 0) atomicAdd(a.mass + inst, m);
     }
     if (!a.keep_grid && lane == 0) a.flags[gw] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_grid(StepArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int n = a.flags[a.n_blocks];
+    const int* list = a.flags + a.n_blocks + 2;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) grid_block(a, list[i], lane);
+    if (list_last_cta(a.flags, a.n_blocks)) {
+        // the mass sums become the totals of this update; without kept grids
+        // the list is emptied for the next substep (every flag is zero again)
+        if (a.mass) {
+            unsigned long long* run = reinterpret_cast<unsigned long long*>(a.mass);
+            for (int i = threadIdx.x; i < a.n_inst; i += blockDim.x)
+                a.mass[a.n_inst + i] = __longlong_as_double((long long)atomicExch(run + i, 0ull));
+        }
+        if (threadIdx.x == 0) {
+            if (!a.keep_grid) a.flags[a.n_blocks] = 0;
+            a.flags[a.n_blocks + 1] = 0;
+        }
+    }
 }
 
 // The 27 nodes of a particle's stencil in the global grid.
@@ -596,15 +635,12 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A)
 #pragma unroll
         for (int k = 0; k < 3; k++) A.adj[(kX + k) * N + p] = gx[k];
     }
-    tile_flush(T, I, A.gacc, nullptr, kChunk);
+    tile_flush(T, I, A.gacc, nullptr, 0, kChunk);
 }
 
-__global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
+// adjoint of the grid update of one touched block gw (one warp)
+__device__ __forceinline__ void grid_bwd_block(const AdjArgs& A, int gw, int lane) {
     const StepArgs& a = A.f;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= a.n_blocks) return;
-    if (a.flags[gw] == 0) return;
     const int inst = a.block_inst[gw];
     const InstDev& I = a.inst[inst];
     const int lb = gw - I.blk_off;
@@ -681,6 +717,15 @@ __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
+    const StepArgs& a = A.f;
+    const int lane = threadIdx.x & 31;
+    const int n = a.flags[a.n_blocks];
+    const int* list = a.flags + a.n_blocks + 2;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) grid_bwd_block(A, list[i], lane);
 }
 
 // spectral data parked in shared memory across the gather (37 words a thread)
@@ -1140,23 +1185,31 @@ __global__ void __launch_bounds__(kFp64Threads) k_p2g_g2p_bwd_fp64(AdjArgs A, Ad
     p2g_bwd_fp64_all<true>(A, &G);
 }
 
+// zero the accumulators (and grid adjoints) of the listed blocks, then the
+// flags and the list
 __global__ void __launch_bounds__(256) k_grid_clear(AdjArgs A) {
     const StepArgs& a = A.f;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (gw >= a.n_blocks) return;
-    if (a.flags[gw] == 0) return;
-    const InstDev& I = a.inst[a.block_inst[gw]];
-    const long long base = I.node_off + (long long)(gw - I.blk_off) * 64;
+    const int n = a.flags[a.n_blocks];
+    const int* list = a.flags + a.n_blocks + 2;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (A.gacc) {
-        A.gacc[base + lane] = z;
-        A.gacc[base + lane + 32] = z;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const int gw = list[i];
+        const InstDev& I = a.inst[a.block_inst[gw]];
+        const long long base = I.node_off + (long long)(gw - I.blk_off) * 64;
+        if (A.gacc) {
+            A.gacc[base + lane] = z;
+            A.gacc[base + lane + 32] = z;
+        }
+        a.acc[base + lane] = z;
+        a.acc[base + lane + 32] = z;
+        if (lane == 0) a.flags[gw] = 0;
     }
-    a.acc[base + lane] = z;
-    a.acc[base + lane + 32] = z;
-    __syncwarp();
-    if (lane == 0) a.flags[gw] = 0;
+    if (list_last_cta(a.flags, a.n_blocks) && threadIdx.x == 0) {
+        a.flags[a.n_blocks] = 0;
+        a.flags[a.n_blocks + 1] = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1244,21 +1297,6 @@ __global__ void __launch_bounds__(kChunk) k_loss_mse(const InstDev* inst, const 
         for (int w = 0; w < kChunk / 32; w++) x += sred[w];
         if (x != 0.0) atomicAdd(loss + ii, x);
     }
-}
-
-// total grid mass per instance after the last grid update (vout.w = m)
-__global__ void __launch_bounds__(256) k_grid_mass(const InstDev* inst, const int* block_inst, int n_blocks,
-                                                   const float4* vout, double* mass) {
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= n_blocks) return;
-    const int ii = block_inst[gw];
-    const InstDev& I = inst[ii];
-    const long long base = I.node_off + (long long)(gw - I.blk_off) * 64;
-    double m = (double)vout[base + lane].w + (double)vout[base + lane + 32].w;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
-    if (lane == 0 && m != 0.0) atomicAdd(mass + ii, m);
 }
 
 // ---------------------------------------------------------------------------
@@ -1415,6 +1453,10 @@ namespace mpm {
 
 static inline int grid_ctas(int n_blocks) { return (n_blocks * 32 + 255) / 256; }
 
+// CTAs of the kernels that walk a block list: a warp per block up to one
+// full wave of 256-thread CTAs (8 per SM), grid-stride beyond
+static inline int list_ctas(int n_blocks) { return std::min(grid_ctas(n_blocks), kListCtas); }
+
 cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
     const StepArgs& a = A.f;
     const bool particle_kernel = id == KernelId::P2G || id == KernelId::G2P || id == KernelId::G2PBwd ||
@@ -1423,16 +1465,16 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
     if ((particle_kernel && a.n_chunks <= 0) || (!particle_kernel && a.n_blocks <= 0)) return cudaSuccess;
     switch (id) {
         case KernelId::P2G: k_p2g<<<a.n_chunks, kChunk, 0, s>>>(a); break;
-        case KernelId::Grid: k_grid<<<grid_ctas(a.n_blocks), 256, 0, s>>>(a); break;
+        case KernelId::Grid: k_grid<<<list_ctas(a.n_blocks), 256, 0, s>>>(a); break;
         case KernelId::G2P: k_g2p<<<a.n_chunks, kChunk, 0, s>>>(a); break;
         case KernelId::G2PBwd: k_g2p_bwd<<<a.n_chunks, kChunk, 0, s>>>(A); break;
-        case KernelId::GridBwd: k_grid_bwd<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
+        case KernelId::GridBwd: k_grid_bwd<<<list_ctas(a.n_blocks), 256, 0, s>>>(A); break;
         case KernelId::P2GBwd:
             if (!a.spec) return cudaErrorInvalidValue;   // needs the recorded SVD
             if (A.gscale) k_p2g_bwd_reg<<<a.n_chunks, kChunk, 0, s>>>(A);
             else k_p2g_bwd<<<a.n_chunks, kChunk, 0, s>>>(A);
             break;
-        case KernelId::GridClear: k_grid_clear<<<grid_ctas(a.n_blocks), 256, 0, s>>>(A); break;
+        case KernelId::GridClear: k_grid_clear<<<list_ctas(a.n_blocks), 256, 0, s>>>(A); break;
         case KernelId::P2GFp64: k_p2g_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(a); break;
         case KernelId::P2GBwdFp64: k_p2g_bwd_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(A); break;
         case KernelId::P2GG2PBwd:
@@ -1440,7 +1482,7 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
         case KernelId::SlotClear: {
             AdjArgs C = A;
             C.gacc = nullptr;
-            k_grid_clear<<<grid_ctas(a.n_blocks), 256, 0, s>>>(C);
+            k_grid_clear<<<list_ctas(a.n_blocks), 256, 0, s>>>(C);
             break;
         }
         default: return cudaErrorInvalidValue;
@@ -1510,13 +1552,6 @@ cudaError_t launch_unpermute(const InstDev* inst, const int* chunk_inst, int n_c
                              const float* src, float* dst, cudaStream_t st) {
     if (n_chunks == 0) return cudaSuccess;
     k_unpermute<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, ncap, perm, src, dst);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_grid_mass(const InstDev* inst, const int* block_inst, int n_blocks, const float4* vout,
-                             double* mass, cudaStream_t st) {
-    if (n_blocks == 0) return cudaSuccess;
-    k_grid_mass<<<grid_ctas(n_blocks), 256, 0, st>>>(inst, block_inst, n_blocks, vout, mass);
     return cudaGetLastError();
 }
 

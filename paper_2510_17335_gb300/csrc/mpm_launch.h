@@ -12,6 +12,7 @@ enum class KernelId : int {
 };
 constexpr int kFp64Ctas = 152;   // CTAs of the FP64 fix-up kernels (grid-stride over the deferred list)
 constexpr int kFp64Threads = 128;
+constexpr int kListCtas = 152 * 8;   // CTAs of the grid kernels that walk the touched-block list
 
 // one substep kernel; forward kernels read only A.f
 cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s);
@@ -39,8 +40,6 @@ constexpr int kSortLaunches = 6;
 // dst[perm[q]] = src[q] for all 24 components
 cudaError_t launch_unpermute(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap, const int* perm,
                              const float* src, float* dst, cudaStream_t st);
-cudaError_t launch_grid_mass(const InstDev* inst, const int* block_inst, int n_blocks, const float4* vout,
-                             double* mass, cudaStream_t st);
 cudaError_t launch_loss_mse(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap,
                             const int* ext_of_slot, const float* s, const float* target, float* dldx, double* loss,
                             cudaStream_t st);

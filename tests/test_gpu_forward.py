@@ -54,6 +54,27 @@ def test_small_bed_10_substeps():
     assert np.isclose(gm[0], w.n * w.rho * w.vol, rtol=1e-6)
 
 
+def test_grid_mass_after_the_bed_leaves_its_blocks():
+    """A uniform translation (v0 constant, C = 0, F = I, no gravity, no
+    shovel) stays a translation under APIC; after 600 substeps the bed has
+    moved 0.15 m in x (more than one 4-cell grid block), so blocks it occupied
+    at the start are empty. The grid mass of the last substep is still
+    sum_p rho V_p: nothing of the vacated blocks is counted."""
+    w = W.cfg_small()
+    v0 = np.array([2.5, 0.0, 1.5], np.float32)
+    nsub = 600
+    with mpm.simulation_from_workloads([w], shovel_on=0, gravity=(0.0, 0.0, 0.0)) as sim:
+        sim.set_state(w.x0, np.tile(v0, (w.n, 1)))
+        sim.forward(nsub)
+        g = sim.get_state()
+        gm = sim.grid_mass()
+    moved = g["x"] - w.x0
+    want = (v0.astype(np.float64) * w.dt * nsub)
+    assert np.abs(moved - want).max() < 1e-4, np.abs(moved - want).max()
+    assert want[0] > 4 * w.dx
+    assert np.isclose(gm[0], w.n * w.rho * w.vol, rtol=1e-6), (gm[0], w.n * w.rho * w.vol)
+
+
 def test_one_step_parity_along_200_substep_trajectory():
     """Every substep of the 200-substep rollout (insert, then push at 10 m/s)
     against the oracle run for one substep from the GPU's own state: the
