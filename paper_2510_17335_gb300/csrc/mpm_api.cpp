@@ -25,10 +25,10 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 
 // touched-block set of one substep (the layout StepArgs::flags describes):
-// n_blocks flags, list length, ticket, n_blocks list entries; the flags and
-// the two counters start at zero, the list needs no initial value
-size_t flag_ints(int n_blocks) { return 2 * (size_t)n_blocks + 2; }
-size_t flag_bytes_zeroed(int n_blocks) { return ((size_t)n_blocks + 2) * sizeof(int); }
+// n_blocks flags, list length, n_blocks list entries; the flags and the
+// length start at zero, the list needs no initial value
+size_t flag_ints(int n_blocks) { return 2 * (size_t)n_blocks + 1; }
+size_t flag_bytes_zeroed(int n_blocks) { return ((size_t)n_blocks + 1) * sizeof(int); }
 
 struct Instance {
     mpm_config cfg;
@@ -150,7 +150,7 @@ struct mpm_handle {
     DevBuf<int> d_chunk_inst, d_block_inst, d_ext_of_slot;
     DevBuf<float> d_state, d_x0, d_stage, d_poses, d_target;
     DevBuf<float4> d_acc, d_vout;
-    DevBuf<int> d_flags;            // touched-block flags, list length, ticket, list (flag_ints)
+    DevBuf<int> d_flags;            // touched-block flags, list length, list (flag_ints)
     DevBuf<double> d_mass;          // grid mass per instance: running sums, last update's totals
     DevBuf<int> d_status;
     DevBuf<unsigned long long> d_fp64;

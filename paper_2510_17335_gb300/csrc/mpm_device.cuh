@@ -920,13 +920,13 @@ __device__ __forceinline__ void tile_add(TileSmem& T, float4* grid, int gofs, co
 // Touched grid blocks of one substep, kept in the int array `flags`:
 //   flags[b] (b < n_blocks)     1 once block b received a P2G contribution
 //   flags[n_blocks]             number of listed blocks
-//   flags[n_blocks + 1]         CTA ticket of the kernel that walks the list
-//   flags[n_blocks + 2 + i]     the i-th listed block, in no particular order
+//   flags[n_blocks + 1 + i]     the i-th listed block, in no particular order
 // The grid kernels walk the list instead of testing every block's flag.
+// The kernel after the one that zeroes the flags (or a memset) empties it.
 __device__ __forceinline__ void mark_block(int* flags, int n_blocks, int b) {
     // test first: the load mostly hits L1; the thread whose exchange sets the
     // flag lists the block
-    if (flags[b] == 0 && atomicExch(flags + b, 1) == 0) flags[n_blocks + 2 + atomicAdd(flags + n_blocks, 1)] = b;
+    if (flags[b] == 0 && atomicExch(flags + b, 1) == 0) flags[n_blocks + 1 + atomicAdd(flags + n_blocks, 1)] = b;
 }
 
 // flush a tile to the global grid (blocked layout of instance I); marks the

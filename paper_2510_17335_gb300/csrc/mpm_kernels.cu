@@ -96,20 +96,6 @@ __device__ __forceinline__ void mark_blocks(const InstDev& I, const Stencil& st,
                 mark_block(flags, n_blocks, I.blk_off + (bx * I.nb[1] + by) * I.nb[2] + bz);
 }
 
-// End of a kernel that walks a block list: true in the last CTA to finish,
-// after every CTA has read the list length on entry (the ticket is in
-// flags[n_blocks + 1]; the caller zeroes it)
-__device__ __forceinline__ bool list_last_cta(int* flags, int n_blocks) {
-    __shared__ int last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(flags + n_blocks + 1, 1) == (int)gridDim.x - 1;
-    }
-    __syncthreads();
-    return last != 0;
-}
-
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
@@ -364,22 +350,23 @@ __device__ __forceinline__ void grid_block(const StepArgs& a, int gw, int lane) 
 __global__ void __launch_bounds__(256) k_grid(StepArgs a) {
     const int lane = threadIdx.x & 31;
     const int n = a.flags[a.n_blocks];
-    const int* list = a.flags + a.n_blocks + 2;
+    const int* list = a.flags + a.n_blocks + 1;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) grid_block(a, list[i], lane);
-    if (list_last_cta(a.flags, a.n_blocks)) {
-        // the mass sums become the totals of this update; without kept grids
-        // the list is emptied for the next substep (every flag is zero again)
-        if (a.mass) {
-            unsigned long long* run = reinterpret_cast<unsigned long long*>(a.mass);
-            for (int i = threadIdx.x; i < a.n_inst; i += blockDim.x)
-                a.mass[a.n_inst + i] = __longlong_as_double((long long)atomicExch(run + i, 0ull));
+}
+
+// Run by the G2P of the same substep, which follows the grid update in stream
+// order: the grid update's mass sums become the totals, and without kept
+// grids the block list is emptied for the next substep (the grid update has
+// zeroed every listed flag).
+__device__ __forceinline__ void grid_epilogue(const StepArgs& a) {
+    if (blockIdx.x != 0) return;
+    if (a.mass)
+        for (int i = threadIdx.x; i < a.n_inst; i += blockDim.x) {
+            a.mass[a.n_inst + i] = a.mass[i];
+            a.mass[i] = 0.0;
         }
-        if (threadIdx.x == 0) {
-            if (!a.keep_grid) a.flags[a.n_blocks] = 0;
-            a.flags[a.n_blocks + 1] = 0;
-        }
-    }
+    if (!a.keep_grid && threadIdx.x == 0) a.flags[a.n_blocks] = 0;
 }
 
 // The 27 nodes of a particle's stencil in the global grid.
@@ -488,6 +475,7 @@ __device__ __forceinline__ void g2p_particle(const InstDev& I, const StepArgs& a
 __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
     __shared__ InstDev sI;
     const int inst = a.chunk_inst[blockIdx.x];
+    grid_epilogue(a);
     const InstDev& I = stage_instance(sI, a.inst, inst);
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
     if (p - I.pbeg >= I.n) return;
@@ -723,7 +711,7 @@ __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
     const StepArgs& a = A.f;
     const int lane = threadIdx.x & 31;
     const int n = a.flags[a.n_blocks];
-    const int* list = a.flags + a.n_blocks + 2;
+    const int* list = a.flags + a.n_blocks + 1;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) grid_bwd_block(A, list[i], lane);
 }
@@ -1102,9 +1090,10 @@ __device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A, const AdjArgs* G) 
             }
         }
     }
-    if (Fused) g2p_bwd_particle(I, *G, inst, p, go_on, true, gxk, gvk, gCk);
+    // parameter sums first: their registers are free for the G2P adjoint
     float gd[4] = {gmu, glam, galpha, gmp};
     block_reduce_add<4>(gd, A.gmat + 4 * inst, sred);
+    if (Fused) g2p_bwd_particle(I, *G, inst, p, go_on, true, gxk, gvk, gCk);
     if (Reg) {
         __syncthreads();   // sred is reused
         block_stat<3>(A.gscale, st, A.pstat_out + 3 * inst, reinterpret_cast<float*>(sred));
@@ -1185,13 +1174,13 @@ __global__ void __launch_bounds__(kFp64Threads) k_p2g_g2p_bwd_fp64(AdjArgs A, Ad
     p2g_bwd_fp64_all<true>(A, &G);
 }
 
-// zero the accumulators (and grid adjoints) of the listed blocks, then the
-// flags and the list
+// zero the accumulators (and grid adjoints) and the flags of the listed
+// blocks (the launcher then empties the list)
 __global__ void __launch_bounds__(256) k_grid_clear(AdjArgs A) {
     const StepArgs& a = A.f;
     const int lane = threadIdx.x & 31;
     const int n = a.flags[a.n_blocks];
-    const int* list = a.flags + a.n_blocks + 2;
+    const int* list = a.flags + a.n_blocks + 1;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
@@ -1205,10 +1194,6 @@ __global__ void __launch_bounds__(256) k_grid_clear(AdjArgs A) {
         a.acc[base + lane] = z;
         a.acc[base + lane + 32] = z;
         if (lane == 0) a.flags[gw] = 0;
-    }
-    if (list_last_cta(a.flags, a.n_blocks) && threadIdx.x == 0) {
-        a.flags[a.n_blocks] = 0;
-        a.flags[a.n_blocks + 1] = 0;
     }
 }
 
@@ -1474,7 +1459,10 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
             if (A.gscale) k_p2g_bwd_reg<<<a.n_chunks, kChunk, 0, s>>>(A);
             else k_p2g_bwd<<<a.n_chunks, kChunk, 0, s>>>(A);
             break;
-        case KernelId::GridClear: k_grid_clear<<<list_ctas(a.n_blocks), 256, 0, s>>>(A); break;
+        case KernelId::GridClear:
+            k_grid_clear<<<list_ctas(a.n_blocks), 256, 0, s>>>(A);
+            if (const cudaError_t e = cudaGetLastError()) return e;
+            return cudaMemsetAsync(a.flags + a.n_blocks, 0, sizeof(int), s);   // empty list
         case KernelId::P2GFp64: k_p2g_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(a); break;
         case KernelId::P2GBwdFp64: k_p2g_bwd_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(A); break;
         case KernelId::P2GG2PBwd:
@@ -1483,7 +1471,8 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
             AdjArgs C = A;
             C.gacc = nullptr;
             k_grid_clear<<<list_ctas(a.n_blocks), 256, 0, s>>>(C);
-            break;
+            if (const cudaError_t e = cudaGetLastError()) return e;
+            return cudaMemsetAsync(a.flags + a.n_blocks, 0, sizeof(int), s);   // empty list
         }
         default: return cudaErrorInvalidValue;
     }

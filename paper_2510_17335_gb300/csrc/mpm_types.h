@@ -58,7 +58,7 @@ struct StepArgs {
     float4* acc;            // P2G accumulators (m, mv) of this substep
     float4* vout;           // grid velocity after the update (xyz), mass (w)
     int* flags;             // grid blocks touched this substep: [n_blocks] flags (0/1), then the
-                            // list length and a CTA ticket, then [n_blocks] the listed blocks
+                            // list length, then [n_blocks] the listed blocks
     int keep_grid;          // 1: the grid kernel leaves acc/flags for the backward
     int n_inst;
     double* mass;           // n_inst running sums, then n_inst totals of the last grid update; may be null

@@ -27,6 +27,7 @@ def _loop(ws, graphs, iters, K, nsub, materials=None):
     MSE loss against a shifted copy of the start, backward."""
     opts = mpm.make_options(checkpoint_every=K, cuda_graphs=graphs)
     out = []
+    theta = np.array([(w.E, w.nu, w.rho, w.phi_deg) for w in ws], np.float64)
     with mpm.simulation_from_workloads(ws, opts) as sim:
         sim.forward(5)
         x0 = sim.get_state()
@@ -35,13 +36,14 @@ def _loop(ws, graphs, iters, K, nsub, materials=None):
             if materials is not None and it in materials:
                 for i, m in enumerate(materials[it]):
                     sim.set_material(i, m)
+                    theta[i] = m
             sim.set_substep(5)
             sim.set_state(x0["x"], x0["v"], x0["C"], x0["F"])
             sim.forward(nsub, record=True)
             L, g = sim.loss_mse(target)
             gm, gt = sim.backward(dL_dx=g)
             out.append((sim.get_state()["x"].copy(), np.asarray(L).copy(), np.asarray(gm).copy(),
-                        sim.state_grad()["F"].copy()))
+                        sim.state_grad()["F"].copy(), theta.copy()))
         info = sim.info()
     return out, info
 
@@ -49,14 +51,23 @@ def _loop(ws, graphs, iters, K, nsub, materials=None):
 def _close(a, b, ref_a, ref_b):
     """Each of (x, L, dL/dmaterial, dL/dF) of run a within 10x the spread of
     two eager runs (ref_a, ref_b) of run b, plus a floor: absolute for the
-    positions, relative per entry for the loss and the material gradient
-    (its four entries span many decades and carry up to ~1e-2 relative
-    summation-order noise on small beds: the gradient bar of the parity
-    tests), relative to the largest entry for dL/dF. A replay that ignored
-    new parameters is caught by the material-change test."""
-    floors = (("abs", 1e-6), ("each", 1e-7), ("each", 2e-2), ("max", 1e-4))
+    positions, relative per entry for the loss, relative to the largest
+    entry for dL/dF. The material gradient is compared as the sensitivities
+    theta_j dL/dtheta_j (E, nu, rho, phi in their units span many decades),
+    with the gradient bar of the parity tests, 2e-2, relative to the
+    instance's largest sensitivity: on small beds a small entry (dL/dphi
+    when few particles yield) is a near-cancelling sum whose float-atomic
+    summation order moves it by a few percent of its own value. A replay
+    that ignored new parameters is caught by the material-change test."""
+    theta = np.asarray(b[4], np.float64)
+    floors = (("abs", 1e-6), ("each", 1e-7), ("sens", 2e-2), ("max", 1e-4))
     for u, v, ru, rv, (kind, fl) in zip(a, b, ref_a, ref_b, floors):
         u, v, ru, rv = (np.asarray(t, np.float64) for t in (u, v, ru, rv))
+        if kind == "sens":
+            u, v, ru, rv = (t * theta for t in (u, v, ru, rv))
+            tol = 10 * np.abs(ru - rv) + fl * np.abs(v).max(axis=1, keepdims=True)
+            assert np.all(np.abs(u - v) <= tol), (u, v, ru, rv)
+            continue
         if kind == "each":
             tol = 10 * np.abs(ru - rv) + fl * np.abs(v)
             assert np.all(np.abs(u - v) <= tol), (u, v, ru, rv)
