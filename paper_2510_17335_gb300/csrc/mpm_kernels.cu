@@ -319,7 +319,7 @@ __device__ __forceinline__ void grid_block(const StepArgs& a, int gw, int lane) 
     float sn, cs;
     sincosf(P.psi, &sn, &cs);
     const long long base = I.node_off + (long long)lb * 64;
-    double m = 0.0;
+    float m = 0.0f;   // the block's mass (FP32 within the block, FP64 across blocks)
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int nd = lane + 32 * h;
@@ -337,12 +337,12 @@ __device__ __forceinline__ void grid_block(const StepArgs& a, int gw, int lane) 
         }
         a.vout[base + nd] = out;
         if (!a.keep_grid) a.acc[base + nd] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        m += (double)acc.x;
+        m += acc.x;
     }
     if (a.mass) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
-        if (lane == 0) atomicAdd(a.mass + inst, m);
+        if (lane == 0) atomicAdd(a.mass + inst, (double)m);
     }
     if (!a.keep_grid && lane == 0) a.flags[gw] = 0;
 }
