@@ -96,6 +96,23 @@ __device__ __forceinline__ void mark_blocks(const InstDev& I, const Stencil& st,
                 mark_block(flags, n_blocks, I.blk_off + (bx * I.nb[1] + by) * I.nb[2] + bz);
 }
 
+// f(gw) for every block of the touched-block list, one warp per entry. A
+// warp's first entry is loaded together with the list length (both written
+// by the kernels before), so that the two loads overlap; entries at or past
+// the length are loaded only within the list's capacity and never used.
+template <class Fn>
+__device__ __forceinline__ void for_listed_blocks(const int* flags, int n_blocks, Fn&& f) {
+    const int* list = flags + n_blocks + 1;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int gw = i < n_blocks ? list[i] : 0;
+    const int n = flags[n_blocks];
+    for (; i < n; i += nw) {
+        f(gw);
+        gw = i + nw < n ? list[i + nw] : 0;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
@@ -349,10 +366,7 @@ __device__ __forceinline__ void grid_block(const StepArgs& a, int gw, int lane) 
 
 __global__ void __launch_bounds__(256) k_grid(StepArgs a) {
     const int lane = threadIdx.x & 31;
-    const int n = a.flags[a.n_blocks];
-    const int* list = a.flags + a.n_blocks + 1;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) grid_block(a, list[i], lane);
+    for_listed_blocks(a.flags, a.n_blocks, [&](int gw) { grid_block(a, gw, lane); });
 }
 
 // Run by the G2P of the same substep, which follows the grid update in stream
@@ -710,10 +724,7 @@ __device__ __forceinline__ void grid_bwd_block(const AdjArgs& A, int gw, int lan
 __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
     const StepArgs& a = A.f;
     const int lane = threadIdx.x & 31;
-    const int n = a.flags[a.n_blocks];
-    const int* list = a.flags + a.n_blocks + 1;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) grid_bwd_block(A, list[i], lane);
+    for_listed_blocks(a.flags, a.n_blocks, [&](int gw) { grid_bwd_block(A, gw, lane); });
 }
 
 // spectral data parked in shared memory across the gather (37 words a thread)
@@ -1179,12 +1190,8 @@ __global__ void __launch_bounds__(kFp64Threads) k_p2g_g2p_bwd_fp64(AdjArgs A, Ad
 __global__ void __launch_bounds__(256) k_grid_clear(AdjArgs A) {
     const StepArgs& a = A.f;
     const int lane = threadIdx.x & 31;
-    const int n = a.flags[a.n_blocks];
-    const int* list = a.flags + a.n_blocks + 1;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
-        const int gw = list[i];
+    for_listed_blocks(a.flags, a.n_blocks, [&](int gw) {
         const InstDev& I = a.inst[a.block_inst[gw]];
         const long long base = I.node_off + (long long)(gw - I.blk_off) * 64;
         if (A.gacc) {
@@ -1194,7 +1201,7 @@ __global__ void __launch_bounds__(256) k_grid_clear(AdjArgs A) {
         a.acc[base + lane] = z;
         a.acc[base + lane + 32] = z;
         if (lane == 0) a.flags[gw] = 0;
-    }
+    });
 }
 
 // ---------------------------------------------------------------------------
