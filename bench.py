@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="shared-memory tile scatter (1) or global atomics (0)")
     ap.add_argument("--sort", type=int, default=0, help="sort particles by cell every n substeps (0: never)")
     ap.add_argument("--batch", type=int, default=64, help="instances of the batched-vs-serial leg (0: skip)")
-    ap.add_argument("--batch-substeps", type=int, default=50)
+    ap.add_argument("--batch-substeps", type=int, default=500, help="substeps of each fwd+bwd loop of the batched leg (the uneven-batch workload runs 500)")
     return ap.parse_args()
 
 
@@ -71,6 +71,22 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(dist, values, device):
+    """Each value's maximum over the ranks (the slowest rank sets the job's
+    time); the values themselves with no process group."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def job_rate(world_size: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed (each rank runs
+    its own replica) over the slowest rank's time."""
+    return world_size * units_per_rank / seconds
 
 
 def measured_peaks():
@@ -360,12 +376,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         fms = f0.elapsed_time(f1)
 
-    t = torch.tensor([ms, fms], device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms, fms = float(t[0]), float(t[1])
-    value = ws * N * S * args.steps / (ms / 1e3)
-    fwd_value = ws * N * S * args.steps / (fms / 1e3)
+    ms, fms = max_over_ranks(dist, [ms, fms], dev)
+    value = job_rate(ws, N * S * args.steps, ms / 1e3)
+    fwd_value = job_rate(ws, N * S * args.steps, fms / 1e3)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -395,12 +408,10 @@ def run_ours(args):
             torch.cuda.synchronize()
             barrier()
             es = time.perf_counter() - t0
-        te = torch.tensor([es], device=dev)
-        if dist is not None:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        (es,) = max_over_ranks(dist, [es], dev)
         h2d = N * 4 * (3 + 3 + 9 + 9) + 2 * N * 3 * 4      # state, target and dL/dx in
         d2h = N * 3 * 4 + 8 * (1 + 4 + 6)                   # dL/dx, loss and gradients out
-        e2e = {"value": ws * N * S * args.steps / float(te[0]), "unit": "particle-substeps/s",
+        e2e = {"value": job_rate(ws, N * S * args.steps, es), "unit": "particle-substeps/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank != 0:
