@@ -636,15 +636,6 @@ int sort_particles(mpm_handle* h, int* perm) {
     return MPM_OK;
 }
 
-int run_adjoint_substep(mpm_handle* h, const AdjArgs& A) {
-    RK(run_kernel(h, KernelId::G2PBwd, A));
-    RK(run_kernel(h, KernelId::GridBwd, A));
-    RK(run_kernel(h, KernelId::P2GBwd, A));
-    RK(run_kernel(h, KernelId::P2GBwdFp64, A));
-    RK(run_kernel(h, KernelId::GridClear, A));
-    return MPM_OK;
-}
-
 }  // namespace
 
 extern "C" {
@@ -1241,24 +1232,40 @@ static int backward_launch(mpm_handle* h, const float* gx, const float* gv, bool
             }
             return A;
         };
+        // With fusion the clearing of substep i+1 (its accumulators, flags
+        // and the grid-adjoint buffer it used) is deferred into the grid
+        // adjoint kernel of substep i, and the particle adjoint kernel after
+        // it empties substep i+1's block list: one launch and one memset
+        // less per substep. Only substep 0 keeps its own clearing launch.
         float4* gcur = h->d_gacc.p;
         float4* goth = h->d_gacc2.p;
         for (int i = seg_len - 1; i >= 0; i--) {
-            const AdjArgs A = args(i, gcur);
+            AdjArgs A = args(i, gcur);
+            const bool defer = fuse && i + 1 < seg_len;   // substep i+1 still to clear
+            if (defer) {
+                A.clr_flags = h->seg_flags[i + 1].p;
+                A.clr_acc = h->seg_acc[i + 1].p;
+                A.clr_gacc = goth;
+                A.reset_list = h->seg_flags[i + 1].p + h->n_blocks;
+            }
             if (!fuse || i == seg_len - 1) RK(run_kernel(h, KernelId::G2PBwd, A));
             RK(run_kernel(h, KernelId::GridBwd, A));
             if (fuse && i > 0) {
                 const AdjArgs G = args(i - 1, goth);
                 RK(run_fused(h, KernelId::P2GG2PBwd, A, G));
                 RK(run_fused(h, KernelId::P2GG2PBwdFp64, A, G));
-                RK(run_kernel(h, KernelId::GridClear, A));
                 std::swap(gcur, goth);
             } else {
                 RK(run_kernel(h, KernelId::P2GBwd, A));
                 RK(run_kernel(h, KernelId::P2GBwdFp64, A));
-                RK(run_kernel(h, KernelId::GridClear, A));
+                AdjArgs C = A;
+                C.clr_flags = nullptr;
+                C.clr_acc = C.clr_gacc = nullptr;
+                C.reset_list = nullptr;
+                RK(run_kernel(h, KernelId::GridClear, C));
+                h->seg_dirty[i] = 0;
             }
-            h->seg_dirty[i] = 0;
+            if (defer) h->seg_dirty[i + 1] = 0;
         }
         h->seg_valid = -1;
         if ((size_t)j < h->seg_sorted.size() && h->seg_sorted[j]) {

@@ -721,10 +721,28 @@ __device__ __forceinline__ void grid_bwd_block(const AdjArgs& A, int gw, int lan
     }
 }
 
+// zero one touched block's accumulators (and grid adjoints) and its flag
+__device__ __forceinline__ void clear_block(const StepArgs& a, int* flags, float4* acc, float4* gacc, int gw,
+                                            int lane) {
+    const InstDev& I = a.inst[a.block_inst[gw]];
+    const long long base = I.node_off + (long long)(gw - I.blk_off) * 64;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gacc) {
+        gacc[base + lane] = z;
+        gacc[base + lane + 32] = z;
+    }
+    acc[base + lane] = z;
+    acc[base + lane + 32] = z;
+    if (lane == 0) flags[gw] = 0;
+}
+
 __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
     const StepArgs& a = A.f;
     const int lane = threadIdx.x & 31;
     for_listed_blocks(a.flags, a.n_blocks, [&](int gw) { grid_bwd_block(A, gw, lane); });
+    if (A.clr_flags)
+        for_listed_blocks(A.clr_flags, a.n_blocks,
+                          [&](int gw) { clear_block(a, A.clr_flags, A.clr_acc, A.clr_gacc, gw, lane); });
 }
 
 // spectral data parked in shared memory across the gather (37 words a thread)
@@ -1042,6 +1060,8 @@ __device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A, const AdjArgs* G) 
     if (threadIdx.x == 0) {
         if (Reg) p2g_bwd_factors(A, inst, sfac);
         else sfac[0] = sfac[1] = sfac[2] = 1.0f;
+        // the grid adjoint kernel before this one has cleared these blocks
+        if (A.reset_list && blockIdx.x == 0) *A.reset_list = 0;
     }
     const InstDev& I = stage_instance(sI, a.inst, inst);
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
@@ -1190,18 +1210,7 @@ __global__ void __launch_bounds__(kFp64Threads) k_p2g_g2p_bwd_fp64(AdjArgs A, Ad
 __global__ void __launch_bounds__(256) k_grid_clear(AdjArgs A) {
     const StepArgs& a = A.f;
     const int lane = threadIdx.x & 31;
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    for_listed_blocks(a.flags, a.n_blocks, [&](int gw) {
-        const InstDev& I = a.inst[a.block_inst[gw]];
-        const long long base = I.node_off + (long long)(gw - I.blk_off) * 64;
-        if (A.gacc) {
-            A.gacc[base + lane] = z;
-            A.gacc[base + lane + 32] = z;
-        }
-        a.acc[base + lane] = z;
-        a.acc[base + lane + 32] = z;
-        if (lane == 0) a.flags[gw] = 0;
-    });
+    for_listed_blocks(a.flags, a.n_blocks, [&](int gw) { clear_block(a, a.flags, a.acc, A.gacc, gw, lane); });
 }
 
 // ---------------------------------------------------------------------------

@@ -89,6 +89,14 @@ struct AdjArgs {
     double* gstat;          // n_inst * 3: grid v-bar after / before the contact, m-bar of substep k,
                             // unregularised (zeroed by the host)
     double* gpose_raw;      // n_inst * 8: the grid kernel's pose adjoint, unregularised
+    // Deferred clearing of the substep reversed just before (fused adjoint):
+    // the grid adjoint kernel also zeroes the accumulators, grid adjoints and
+    // flags of the blocks listed in clr_flags; the particle adjoint kernel
+    // after it empties that list (*reset_list = 0). Null: nothing deferred.
+    int* clr_flags;
+    float4* clr_acc;
+    float4* clr_gacc;
+    int* reset_list;
 };
 
 }  // namespace mpm
