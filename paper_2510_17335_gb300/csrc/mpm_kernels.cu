@@ -265,14 +265,16 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_P2G) k_p2g(StepArgs a) {
 
 // Deferred-list bookkeeping of the FP64 fix-up kernels: every CTA reads the
 // count, and the last CTA to finish zeroes the count and the ticket for the
-// next launch (stream order keeps the next producer behind it).
+// next launch (stream order keeps the next producer behind it). With an
+// empty list (the usual case) no CTA takes a ticket: all read the same zero.
 __device__ __forceinline__ int fb_begin(const int* fb_count, int* scount) {
     if (threadIdx.x == 0) *scount = *(volatile const int*)fb_count;
     __syncthreads();
     return *scount;
 }
 
-__device__ __forceinline__ void fb_end(int* fb_count) {
+__device__ __forceinline__ void fb_end(int* fb_count, int count) {
+    if (count == 0) return;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(kFp64Threads) k_p2g_fp64(StepArgs a) {
         mark_blocks(I, st, a.flags, a.n_blocks);
         atomicAdd(a.fp64_count, 1ull);
     }
-    fb_end(a.fb_count);
+    fb_end(a.fb_count, count);
 }
 
 // velocity update of one node (gravity, walls); returns false for empty nodes
@@ -1196,7 +1198,7 @@ __device__ __forceinline__ void p2g_bwd_fp64_all(const AdjArgs& A, const AdjArgs
         atomicAdd(A.gmat + 4 * inst + 3, (double)gmp);
         atomicAdd(a.fp64_count, 1ull);
     }
-    fb_end(a.fb_count);
+    fb_end(a.fb_count, count);
 }
 
 __global__ void __launch_bounds__(kFp64Threads) k_p2g_bwd_fp64(AdjArgs A) { p2g_bwd_fp64_all<false>(A, nullptr); }
