@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="shared-memory tile scatter (1) or global atomics (0)")
     ap.add_argument("--sort", type=int, default=0, help="sort particles by cell every n substeps (0: never)")
     ap.add_argument("--batch", type=int, default=64, help="instances of the batched-vs-serial leg (0: skip)")
+    ap.add_argument("--sysid", type=int, default=0,
+                    help="candidates of the system-identification leg (0: skip; it takes minutes)")
+    ap.add_argument("--sysid-substeps", type=int, default=300)
+    ap.add_argument("--sysid-iters", type=int, default=30)
     ap.add_argument("--batch-substeps", type=int, default=500, help="substeps of each fwd+bwd loop of the batched leg (the uneven-batch workload runs 500)")
     return ap.parse_args()
 
@@ -276,6 +280,35 @@ def batched_vs_serial(n_inst: int, nsub: int, steps: int, sort_every: int):
 
 
 # --------------------------------------------------------------------------
+# system identification: wall clock to 5% parameter error, batched vs serial
+# --------------------------------------------------------------------------
+def sysid_leg(n_cand: int, nsub: int, iters: int):
+    import numpy as np
+
+    from paper_2510_17335_gb300 import mpm, sysid
+    from paper_2510_17335_gb300 import workloads as W
+
+    w = W.cfg_sysid(n_substeps=nsub)
+    rng = np.random.default_rng(W.SEED_BASE + 6)
+    truth = (w.E, w.nu, w.rho, w.phi_deg)
+    free = (True, False, False, True)               # E and phi; nu, rho known
+    starts = [(rng.uniform(*sysid.RANGES[0]), w.nu, w.rho, rng.uniform(*sysid.RANGES[3])) for _ in range(n_cand)]
+    grid = mpm.make_obs_grid((0.5, 0.5), 0.5, 40)
+    out = {"candidates": n_cand, "particles_per_candidate": w.n, "grid": "64^3", "substeps": nsub,
+           "free": ["E", "phi"], "truth": list(truth), "line_search": "hmd (5 multiples, Sec. III-F)",
+           "optimiser": "RMSprop beta 0.9, step sizes E 1e4, phi 1; adjoint clipping 1e4"}
+    for mode in ("batched", "serial"):
+        r = sysid.identify(w, truth, starts, nsub, iters, grid, free=free, batched=(mode == "batched"))
+        out[mode] = {"iterations_to_5pct": r.converged_at, "seconds_to_5pct": r.seconds_to_converge,
+                     "seconds_per_iteration": r.seconds[-1] / len(r.seconds),
+                     "final_max_rel_error": float(np.max(r.errors[-1])),
+                     "final_params": np.round(r.params[-1], 4).tolist()}
+    b, s_ = out["batched"]["seconds_per_iteration"], out["serial"]["seconds_per_iteration"]
+    out["speedup_per_iteration"] = s_ / b
+    return out
+
+
+# --------------------------------------------------------------------------
 # our implementation
 # --------------------------------------------------------------------------
 def auto_checkpoint(S: int, slot_state: int, slot_grid: int, free_bytes: int) -> int:
@@ -457,6 +490,7 @@ def run_ours(args):
     batch = None
     if args.batch > 0:
         batch = batched_vs_serial(args.batch, args.batch_substeps, 3, args.sort)
+    sid = sysid_leg(args.sysid, args.sysid_substeps, args.sysid_iters) if args.sysid > 0 else None
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         r, secs, desc = oracle_sample(w, 24, 40, args.start)   # about 12 s on one core
@@ -475,6 +509,7 @@ def run_ours(args):
         "fwd_value": fwd_value, "fwd_ms_per_step": fms / args.steps,
         "roofline": roof, "alu": alu, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "batched_vs_serial": batch,
+        **({"sysid": sid} if sid is not None else {}),
         "kernels": kernels, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -1,0 +1,167 @@
+"""System identification of Sec. III-F / IV-B on the batched simulator.
+
+Candidates of the material parameters (E, nu, rho, phi) run as instances of
+one handle (or, for comparison, one handle each). Every iteration records a
+rollout, takes the MSE of the final positions against the target cloud and
+its adjoint (with the adjoint clipping of Sec. III-E), makes an RMSprop step
+(beta = 0.9) with the paper's step sizes, and picks the step length by the
+line search of Sec. III-F: five multiples of the step run as one batched
+forward and the one with the least height-map distance to the target map
+wins. The host only orchestrates; every rollout, loss, adjoint and height
+map runs in the library's kernels.
+
+Under a kinematic shovel the motion depends on E and rho only through E/rho
+(the momentum balance divided by the density), so positions identify the
+ratio, not both: rho is held at a known value unless it is freed.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import mpm
+
+# step sizes of Sec. IV-B (E [Pa], nu, rho [kg/m^3], phi [deg]) and the
+# parameter ranges of the same table, used to keep candidates valid
+STEP = (1e4, 0.01, 50.0, 1.0)
+RANGES = ((5e4, 2e5), (0.1, 0.4), (1200.0, 2200.0), (10.0, 40.0))
+ALPHAS = (0.1, 0.5, 1.0, 1.5, 2.0)    # line-search multiples (Sec. III-F)
+BETA = 0.9                            # RMSprop decay
+
+
+@dataclass
+class SysIdResult:
+    params: np.ndarray                  # [iterations + 1, n_cand, 4]
+    losses: List[np.ndarray] = field(default_factory=list)   # MSE per iteration, [n_cand]
+    errors: List[np.ndarray] = field(default_factory=list)   # max relative error of the free parameters
+    seconds: List[float] = field(default_factory=list)       # wall clock at the end of each iteration
+    converged_at: Optional[int] = None  # first iteration after which every candidate is within tol
+    seconds_to_converge: Optional[float] = None
+
+
+def _clamp(theta: np.ndarray) -> np.ndarray:
+    lo = np.array([r[0] for r in RANGES])
+    hi = np.array([r[1] for r in RANGES])
+    return np.minimum(np.maximum(theta, lo), hi)
+
+
+def _auto_checkpoint(n_substeps: int, n_particles: int, n_nodes: int) -> int:
+    """The largest checkpoint interval <= n_substeps whose recorded segment
+    (a state and the recorded SVD per particle, the grids per node, for every
+    substep of the segment) takes at most half the free device memory."""
+    import torch
+    per_slot = 192 * n_particles + 32 * n_nodes + n_nodes // 8
+    k = (torch.cuda.mem_get_info()[0] // 2 - 96 * n_particles) // max(per_slot, 1)
+    return int(max(1, min(n_substeps, k)))
+
+
+def _rel_error(theta: np.ndarray, truth: np.ndarray, free: np.ndarray) -> np.ndarray:
+    e = np.abs(theta - truth) / np.abs(truth)
+    return np.where(free[None, :], e, 0.0).max(axis=1)
+
+
+class _Group:
+    """Handles of one group of candidates: the gradient handle (one instance
+    per candidate) and the line-search handle (one instance per candidate and
+    step multiple)."""
+
+    def __init__(self, w, n_cand: int, n_substeps: int, options):
+        self.n_cand = n_cand
+        self.grad = mpm.simulation_from_workloads([w] * n_cand, options)
+        self.ls = mpm.simulation_from_workloads([w] * (n_cand * len(ALPHAS)), options)
+        self.n_substeps = n_substeps
+
+    def close(self):
+        self.grad.close()
+        self.ls.close()
+
+
+def identify(w, truth: Sequence[float], starts: Sequence[Sequence[float]], n_substeps: int, iterations: int,
+             grid: "mpm.mpm_obs_grid", free=(True, True, False, True), tol: float = 0.05, batched: bool = True,
+             checkpoint_every: int = 0, clip_value: float = 1e4, line_search: str = "hmd") -> SysIdResult:
+    """Identify the material of workload w from the final state of a rollout
+    with the hidden material `truth`, starting every candidate from
+    starts[c]; batched: all candidates in one handle, else one handle each
+    (the serial path, same arithmetic). line_search: "hmd" ranks the step
+    multiples by the height-map distance to the target map (Sec. III-F),
+    "mse" by the position loss the gradient descends. checkpoint_every 0:
+    the largest interval whose recorded segment fits half the free device
+    memory (the whole rollout when it fits). Returns the parameter
+    history and the wall clock to bring every candidate within `tol`
+    relative error on the free parameters (None if it never did)."""
+    if line_search not in ("hmd", "mse"):
+        raise ValueError("line_search must be 'hmd' or 'mse'")
+    import torch
+
+    truth = np.asarray(truth, np.float64)
+    theta = _clamp(np.asarray(starts, np.float64).reshape(-1, 4).copy())
+    n_cand = theta.shape[0]
+    free = np.asarray(free, bool)
+    nodes = int(np.prod([-(-r // 4) * 4 for r in w.res]))
+    k = checkpoint_every or _auto_checkpoint(n_substeps, n_cand * w.n, n_cand * nodes)
+    opts = mpm.make_options(checkpoint_every=k, clip_grads=1, clip_value=clip_value)
+
+    # target cloud and height map from the hidden material
+    with mpm.simulation_from_workloads([w], opts) as ref:
+        ref.set_material(0, truth)
+        ref.forward(n_substeps)
+        x_target = ref.get_state()["x"]
+        map_target = ref.height_map(grid)[0]
+
+    groups = [_Group(w, n_cand, n_substeps, opts)] if batched else [_Group(w, 1, n_substeps, opts)
+                                                                    for _ in range(n_cand)]
+    members = [list(range(n_cand))] if batched else [[c] for c in range(n_cand)]
+    io = []
+    for g, mem in zip(groups, members):
+        tgt = torch.from_numpy(np.tile(x_target, (len(mem), 1))).cuda()
+        ls_tgt = torch.from_numpy(np.tile(x_target, (len(mem) * len(ALPHAS), 1))).cuda()
+        io.append((tgt, torch.empty_like(tgt), np.tile(map_target, (len(mem) * len(ALPHAS), 1, 1)), ls_tgt))
+
+    res = SysIdResult(params=np.zeros((iterations + 1, n_cand, 4)))
+    res.params[0] = theta
+    msq = np.zeros((n_cand, 4))
+    t0 = time.perf_counter()
+    try:
+        for it in range(iterations):
+            L_all = np.zeros(n_cand)
+            for g, mem, (tgt, dl, maps, ls_tgt) in zip(groups, members, io):
+                # gradient of the position loss at the current candidates
+                for k, c in enumerate(mem):
+                    g.grad.set_material(k, theta[c])
+                g.grad.reset()
+                g.grad.forward(n_substeps, record=True)
+                L, _ = g.grad.loss_mse(tgt, grad_out=dl)
+                gm, _ = g.grad.backward(dL_dx=dl)
+                L_all[mem] = L
+                # RMSprop direction with the paper's step sizes
+                gm = np.where(free[None, :], gm, 0.0)
+                msq[mem] = BETA * msq[mem] + (1.0 - BETA) * gm * gm
+                step = np.asarray(STEP)[None, :] * gm / (np.sqrt(msq[mem]) + 1e-30)
+                # line search: every candidate at every multiple, one forward
+                trial = np.stack([_clamp(theta[mem] - a * step) for a in ALPHAS], axis=1)   # [m, 5, 4]
+                for k in range(len(mem)):
+                    for j in range(len(ALPHAS)):
+                        g.ls.set_material(k * len(ALPHAS) + j, trial[k, j])
+                g.ls.reset()
+                g.ls.forward(n_substeps)
+                if line_search == "hmd":
+                    score, _ = g.ls.loss_hmd(grid, maps, want_grad=False)
+                else:
+                    score, _ = g.ls.loss_mse(ls_tgt, want_grad=False)
+                best = score.reshape(len(mem), len(ALPHAS)).argmin(axis=1)   # ties: the smaller multiple
+                theta[mem] = trial[np.arange(len(mem)), best]
+            res.params[it + 1] = theta
+            res.losses.append(L_all)
+            err = _rel_error(theta, truth, free)
+            res.errors.append(err)
+            res.seconds.append(time.perf_counter() - t0)
+            if res.converged_at is None and (err < tol).all():
+                res.converged_at = it + 1
+                res.seconds_to_converge = res.seconds[-1]
+    finally:
+        for g in groups:
+            g.close()
+    return res

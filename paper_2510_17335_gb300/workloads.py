@@ -195,6 +195,25 @@ def batch_uneven(n_inst: int = 64, seed: int = SEED_BASE + 4, n_lo: float = 2e4,
     return out
 
 
+def cfg_sysid(seed: int = SEED_BASE + 5, n_substeps: int = 1500) -> Workload:
+    """The batched system-identification workload's bed: 98,304 particles
+    (32 x 12 x 32 cells at 8 per cell) on a 64^3 grid, dt 5e-5; the shovel tip
+    starts at the bed surface, a quarter along x, and is scripted to insert
+    then push, each by 0.05 m per 1,500 substeps (about 1.3 m/s). Hidden
+    material E 1.2e5, nu 0.3, rho 1600, phi 32 deg (inside the ranges of
+    Sec. IV-B)."""
+    res, dx = (64, 64, 64), 1.0 / 64
+    cells = (32, 12, 32)
+    x0, (ox, oy, oz) = _centred_bed(seed, res, dx, cells)
+    top = oy + cells[1] * dx
+    half = max(1, n_substeps // 20)                 # actions of 10 substeps per phase
+    d = 0.05 * n_substeps / 1500.0
+    traj = Trajectory(start_pose=(ox + 0.25 * cells[0] * dx, top, 0.5, 0.0), substeps_per_action=10,
+                      actions=insert_push_actions(half, d, d))
+    return Workload(f"sysid_n{x0.shape[0]}_grid64", res, dx, 5e-5, n_substeps, 1.2e5, 0.3, 1600.0, 32.0,
+                    dx ** 3 / 8, x0, traj)
+
+
 def tiny(seed: int, n_side: int = 3, res: int = 12, jitter: float = 0.25) -> np.ndarray:
     """A small cube of n_side^3 particles in the middle of a res^3 grid."""
     dx = 1.0 / res

@@ -121,3 +121,19 @@ def test_clipping_bounds_the_adjoints():
     # the returned adjoints are one substep past the last clip; bounded by a
     # small multiple of the clip value times the substep's Jacobian norm
     assert np.abs(g["x"]).max() < np.abs(g0["x"]).max()
+
+
+@pytest.mark.parametrize("name", ["elastic", "plastic", "contact", "walls"])
+def test_material_gradient_is_invariant_under_scaling_E_and_rho(name):
+    """Scaling E and rho by the same factor scales the stresses (mu and
+    lambda are linear in E) and the particle masses alike; the grid velocity
+    is their quotient, so no trajectory changes, and a loss of the state has
+    E dL/dE + rho dL/drho = 0. The two terms come through different chains
+    (mu, lambda and the stress adjoint; m_p = rho V_p and the transfer
+    adjoint), so a wrong factor in either breaks the identity."""
+    p, st, poses, w = _scenario(name)
+    status, g = oracle.rollout_adjoint(p, st["x"], st["v"], st["C"], st["F"], poses, **w)
+    assert status == 0
+    tE, trho = p.E * g["material"][0], p.rho * g["material"][2]
+    assert abs(tE) > 0
+    assert abs(tE + trho) <= 1e-9 * max(abs(tE), abs(trho)), (tE, trho)
