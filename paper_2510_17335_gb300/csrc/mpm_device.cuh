@@ -917,6 +917,12 @@ __device__ __forceinline__ void tile_add(TileSmem& T, float4* grid, int gofs, co
     }
 }
 
+// Programmatic dependent launch: the kernels of the substep path may be
+// scheduled while the previous kernel in the stream is finishing; each of
+// them calls this first, which returns once that grid has completed and its
+// memory writes are visible (a no-op for a kernel launched normally).
+__device__ __forceinline__ void wait_previous_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Touched grid blocks of one substep, kept in the int array `flags`:
 //   flags[b] (b < n_blocks)     1 once block b received a P2G contribution
 //   flags[n_blocks]             number of listed blocks

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "mpm_device.cuh"
 #include "mpm_launch.h"
@@ -26,6 +27,10 @@
 // defaults are the fastest of a measured sweep on the 1M-particle bed)
 #ifndef MPM_MINB_P2G
 #define MPM_MINB_P2G 4
+#endif
+// 1: the substep kernels use programmatic dependent launch (launch_pdl)
+#ifndef MPM_PDL
+#define MPM_PDL 1
 #endif
 #ifndef MPM_MINB_G2P
 #define MPM_MINB_G2P 4
@@ -224,6 +229,7 @@ __device__ __forceinline__ void p2g_store_affine(const InstDev& I, const StepArg
 // ill-conditioned for FP32 (see needs_fp64) is listed for k_p2g_fp64, which
 // does its constitutive step and transfer.
 __global__ void __launch_bounds__(kChunk, MPM_MINB_P2G) k_p2g(StepArgs a) {
+    wait_previous_grid();
     __shared__ TileSmem T;
     __shared__ InstDev sI;
     const int inst = a.chunk_inst[blockIdx.x];
@@ -288,6 +294,7 @@ __device__ __forceinline__ void fb_end(int* fb_count, int count) {
 // The particles k_p2g listed: constitutive step in FP64, transfer with
 // global atomics.
 __global__ void __launch_bounds__(kFp64Threads) k_p2g_fp64(StepArgs a) {
+    wait_previous_grid();
     __shared__ int scount;
     const int count = fb_begin(a.fb_count, &scount);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
@@ -367,6 +374,7 @@ __device__ __forceinline__ void grid_block(const StepArgs& a, int gw, int lane) 
 }
 
 __global__ void __launch_bounds__(256) k_grid(StepArgs a) {
+    wait_previous_grid();
     const int lane = threadIdx.x & 31;
     for_listed_blocks(a.flags, a.n_blocks, [&](int gw) { grid_block(a, gw, lane); });
 }
@@ -489,6 +497,7 @@ __device__ __forceinline__ void g2p_particle(const InstDev& I, const StepArgs& a
 }
 
 __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
+    wait_previous_grid();
     __shared__ InstDev sI;
     const int inst = a.chunk_inst[blockIdx.x];
     grid_epilogue(a);
@@ -559,6 +568,7 @@ __device__ __forceinline__ void g2p_bwd_scatter(const InstDev& I, const AdjArgs&
 }
 
 __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A) {
+    wait_previous_grid();
     __shared__ TileSmem T;
     __shared__ InstDev sI;
     __shared__ float sfac[2];
@@ -739,6 +749,7 @@ __device__ __forceinline__ void clear_block(const StepArgs& a, int* flags, float
 }
 
 __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
+    wait_previous_grid();
     const StepArgs& a = A.f;
     const int lane = threadIdx.x & 31;
     for_listed_blocks(a.flags, a.n_blocks, [&](int gw) { grid_bwd_block(A, gw, lane); });
@@ -1134,10 +1145,12 @@ __device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A, const AdjArgs* G) 
 }
 
 __global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd(AdjArgs A) {
+    wait_previous_grid();
     p2g_bwd_cta<false, false>(A, nullptr);
 }
 
 __global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd_reg(AdjArgs A) {
+    wait_previous_grid();
     p2g_bwd_cta<true, false>(A, nullptr);
 }
 
@@ -1145,6 +1158,7 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd_reg(AdjArg
 // one pass over the particles: the x, v, C adjoints of state k stay in
 // registers. G.gacc is the other grid-adjoint buffer (zero on entry).
 __global__ void __launch_bounds__(kChunk, MPM_MINB_FUSED_BWD) k_p2g_g2p_bwd(AdjArgs A, AdjArgs G) {
+    wait_previous_grid();
     p2g_bwd_cta<false, true>(A, &G);
 }
 
@@ -1201,15 +1215,20 @@ __device__ __forceinline__ void p2g_bwd_fp64_all(const AdjArgs& A, const AdjArgs
     fb_end(a.fb_count, count);
 }
 
-__global__ void __launch_bounds__(kFp64Threads) k_p2g_bwd_fp64(AdjArgs A) { p2g_bwd_fp64_all<false>(A, nullptr); }
+__global__ void __launch_bounds__(kFp64Threads) k_p2g_bwd_fp64(AdjArgs A) {
+    wait_previous_grid();
+    p2g_bwd_fp64_all<false>(A, nullptr);
+}
 
 __global__ void __launch_bounds__(kFp64Threads) k_p2g_g2p_bwd_fp64(AdjArgs A, AdjArgs G) {
+    wait_previous_grid();
     p2g_bwd_fp64_all<true>(A, &G);
 }
 
 // zero the accumulators (and grid adjoints) and the flags of the listed
 // blocks (the launcher then empties the list)
 __global__ void __launch_bounds__(256) k_grid_clear(AdjArgs A) {
+    wait_previous_grid();
     const StepArgs& a = A.f;
     const int lane = threadIdx.x & 31;
     for_listed_blocks(a.flags, a.n_blocks, [&](int gw) { clear_block(a, a.flags, a.acc, A.gacc, gw, lane); });
@@ -1456,6 +1475,31 @@ namespace mpm {
 
 static inline int grid_ctas(int n_blocks) { return (n_blocks * 32 + 255) / 256; }
 
+// Launch of a kernel of the substep path with programmatic stream
+// serialization: its CTAs may be scheduled as the previous kernel's last
+// CTAs retire (hiding the launch gap); every such kernel waits at its start
+// (wait_previous_grid) until the previous grid has completed and its writes
+// are visible, so the stream order of the results is unchanged.
+template <typename... P, typename... A>
+static cudaError_t launch_pdl(void (*k)(P...), unsigned grid, unsigned block, cudaStream_t s, A&&... args) {
+#if MPM_PDL
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+#else
+    k<<<grid, block, 0, s>>>(std::forward<A>(args)...);
+    return cudaGetLastError();
+#endif
+}
+
 // CTAs of the kernels that walk a block list: a warp per block up to one
 // full wave of 256-thread CTAs (8 per SM), grid-stride beyond
 static inline int list_ctas(int n_blocks) { return std::min(grid_ctas(n_blocks), kListCtas); }
@@ -1467,29 +1511,25 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
                                  id == KernelId::P2GBwdFp64;
     if ((particle_kernel && a.n_chunks <= 0) || (!particle_kernel && a.n_blocks <= 0)) return cudaSuccess;
     switch (id) {
-        case KernelId::P2G: k_p2g<<<a.n_chunks, kChunk, 0, s>>>(a); break;
-        case KernelId::Grid: k_grid<<<list_ctas(a.n_blocks), 256, 0, s>>>(a); break;
-        case KernelId::G2P: k_g2p<<<a.n_chunks, kChunk, 0, s>>>(a); break;
-        case KernelId::G2PBwd: k_g2p_bwd<<<a.n_chunks, kChunk, 0, s>>>(A); break;
-        case KernelId::GridBwd: k_grid_bwd<<<list_ctas(a.n_blocks), 256, 0, s>>>(A); break;
+        case KernelId::P2G: return launch_pdl(k_p2g, a.n_chunks, kChunk, s, a);
+        case KernelId::Grid: return launch_pdl(k_grid, list_ctas(a.n_blocks), 256, s, a);
+        case KernelId::G2P: return launch_pdl(k_g2p, a.n_chunks, kChunk, s, a);
+        case KernelId::G2PBwd: return launch_pdl(k_g2p_bwd, a.n_chunks, kChunk, s, A);
+        case KernelId::GridBwd: return launch_pdl(k_grid_bwd, list_ctas(a.n_blocks), 256, s, A);
         case KernelId::P2GBwd:
             if (!a.spec) return cudaErrorInvalidValue;   // needs the recorded SVD
-            if (A.gscale) k_p2g_bwd_reg<<<a.n_chunks, kChunk, 0, s>>>(A);
-            else k_p2g_bwd<<<a.n_chunks, kChunk, 0, s>>>(A);
-            break;
+            return launch_pdl(A.gscale ? k_p2g_bwd_reg : k_p2g_bwd, a.n_chunks, kChunk, s, A);
         case KernelId::GridClear:
-            k_grid_clear<<<list_ctas(a.n_blocks), 256, 0, s>>>(A);
-            if (const cudaError_t e = cudaGetLastError()) return e;
+            if (const cudaError_t e = launch_pdl(k_grid_clear, list_ctas(a.n_blocks), 256, s, A)) return e;
             return cudaMemsetAsync(a.flags + a.n_blocks, 0, sizeof(int), s);   // empty list
-        case KernelId::P2GFp64: k_p2g_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(a); break;
-        case KernelId::P2GBwdFp64: k_p2g_bwd_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(A); break;
+        case KernelId::P2GFp64: return launch_pdl(k_p2g_fp64, kFp64Ctas, kFp64Threads, s, a);
+        case KernelId::P2GBwdFp64: return launch_pdl(k_p2g_bwd_fp64, kFp64Ctas, kFp64Threads, s, A);
         case KernelId::P2GG2PBwd:
         case KernelId::P2GG2PBwdFp64: return cudaErrorInvalidValue;   // two argument sets: launch_fused
         case KernelId::SlotClear: {
             AdjArgs C = A;
             C.gacc = nullptr;
-            k_grid_clear<<<list_ctas(a.n_blocks), 256, 0, s>>>(C);
-            if (const cudaError_t e = cudaGetLastError()) return e;
+            if (const cudaError_t e = launch_pdl(k_grid_clear, list_ctas(a.n_blocks), 256, s, C)) return e;
             return cudaMemsetAsync(a.flags + a.n_blocks, 0, sizeof(int), s);   // empty list
         }
         default: return cudaErrorInvalidValue;
@@ -1502,8 +1542,8 @@ cudaError_t launch_fused(KernelId id, const AdjArgs& A, const AdjArgs& G, cudaSt
     if (a.n_chunks <= 0) return cudaSuccess;
     if (!a.spec || A.gscale || a.tile) return cudaErrorInvalidValue;
     switch (id) {
-        case KernelId::P2GG2PBwd: k_p2g_g2p_bwd<<<a.n_chunks, kChunk, 0, s>>>(A, G); break;
-        case KernelId::P2GG2PBwdFp64: k_p2g_g2p_bwd_fp64<<<kFp64Ctas, kFp64Threads, 0, s>>>(A, G); break;
+        case KernelId::P2GG2PBwd: return launch_pdl(k_p2g_g2p_bwd, a.n_chunks, kChunk, s, A, G);
+        case KernelId::P2GG2PBwdFp64: return launch_pdl(k_p2g_g2p_bwd_fp64, kFp64Ctas, kFp64Threads, s, A, G);
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
