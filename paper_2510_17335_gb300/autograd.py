@@ -42,14 +42,16 @@ class _Rollout(torch.autograd.Function):
         x = torch.empty((sim.n, 3), device="cuda", dtype=torch.float32)
         sim.get_state(device_out={"x": x})
         ctx.sim = sim
-        ctx.dev = materials.device
+        ctx.mat = (materials.device, materials.dtype)
+        ctx.th = (thetas.device, thetas.dtype)
         return x
 
     @staticmethod
     def backward(ctx, gx):
         gm, gt = ctx.sim.backward(dL_dx=gx.contiguous().float())
-        gmt = torch.from_numpy(gm).to(ctx.dev)
-        gtt = torch.from_numpy(gt).to(ctx.dev)
+        # the FP64 sums of the library, in each input's device and dtype
+        gmt = torch.from_numpy(gm).to(device=ctx.mat[0], dtype=ctx.mat[1])
+        gtt = torch.from_numpy(gt).to(device=ctx.th[0], dtype=ctx.th[1])
         return gmt, gtt, None, None, None
 
 
