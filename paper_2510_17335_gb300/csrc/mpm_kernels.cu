@@ -51,16 +51,18 @@ __device__ __forceinline__ float ld(const float* s, long long ncap, int comp, lo
     return s[comp * ncap + p];
 }
 
-// a[i] through selects: the stencil loops over i stay rolled (code size),
-// and a runtime index would move the whole stencil into local memory
+// a[i] through selects: where a stencil loop over i stays rolled (the P2G
+// scatter and the P2G adjoint's gather; unrolled they spill more and run
+// slower), a runtime index would move the whole stencil into local memory
 template <typename T>
 __device__ __forceinline__ T sel3(const T (&a)[3], int i) {
     return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]);
 }
 
 // The x-axis weights, weight derivatives and node offsets of a stencil as a
-// small array that the rolled loop over i indexes at run time (it lives in
-// local memory; the rest of the stencil stays in registers).
+// small array that a rolled loop over i indexes at run time (it lives in
+// local memory; the rest of the stencil stays in registers). Fully unrolled
+// loops index it at compile time and keep it in registers.
 struct AxisX {
     float w[3], dw[3];
     int o[3];
@@ -418,7 +420,7 @@ __device__ __forceinline__ void g2p_gather(const Stencil& st, const Nodes& src, 
     float wzd[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) wzd[k] = st.w[2][k] * (float(k) - st.fx[2]);
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < 3; i++) {
         const float di = float(i) - st.fx[0];
         const float wx = sel3(st.w[0], i);
@@ -529,7 +531,7 @@ __device__ __forceinline__ void g2p_bwd_scatter(const InstDev& I, const AdjArgs&
     float Sv[3] = {0.f, 0.f, 0.f};
     float4* ga = A.gacc + I.node_off;
     const AxisX lx = axis_x(st, ox);
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < 3; i++) {
         const float wx = lx.w[i], dwx = lx.dw[i], dxi = (float(i) - st.fx[0]) * I.dx;
         float bi[3];
