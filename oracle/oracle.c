@@ -68,10 +68,6 @@ static void mmt(const double* A, const double* B, double* C) {
         }
     memcpy(C, T, sizeof T);
 }
-static double det3(const double* A) {
-    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
-           A[2] * (A[3] * A[7] - A[4] * A[6]);
-}
 /* U diag(d) V^T */
 static void udvt(const double* U, const double* d, const double* V, double* out) {
     for (int i = 0; i < 3; i++)
