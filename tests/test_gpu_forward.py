@@ -75,6 +75,37 @@ def test_grid_mass_after_the_bed_leaves_its_blocks():
     assert np.isclose(gm[0], w.n * w.rho * w.vol, rtol=1e-6), (gm[0], w.n * w.rho * w.vol)
 
 
+def test_angular_momentum_conserved_on_the_gpu():
+    """The APIC angular momentum (with its affine part, m_p eps : (C D)^T,
+    D = dx^2/4 I) is constant over a rollout without gravity, walls or
+    shovel, plastic flow included (the Kirchhoff stress is symmetric); on
+    the GPU to FP32 rounding."""
+    rng = np.random.default_rng(4)
+    w = W.cfg_small()
+    n = w.n
+    x = (w.x0 + np.array([0.0, 0.2, 0.0], np.float32)).astype(np.float32)   # off the floor's wall zone
+    ctr = x.mean(0)
+    v = (np.cross(np.array([3.0, -5.0, 8.0]), x - ctr) + rng.normal(size=(n, 3)) * 0.05).astype(np.float32)
+    C = (rng.normal(size=(n, 3, 3)) * 2.0).astype(np.float32)
+    F = W.strained_F(rng, n, 0.05, (0.02, -0.08, 0.01)).astype(np.float32)
+
+    def L(x, v, C):
+        x, v, C = (np.asarray(a, np.float64) for a in (x, v, C))
+        aff = np.stack([C[:, 2, 1] - C[:, 1, 2], C[:, 0, 2] - C[:, 2, 0], C[:, 1, 0] - C[:, 0, 1]], axis=1)
+        return np.cross(x, v).sum(0) + 0.25 * w.dx ** 2 * aff.sum(0), \
+            np.abs(np.cross(x, v)).sum() + 0.25 * w.dx ** 2 * np.abs(C).sum()
+
+    with mpm.simulation_from_workloads([w], shovel_on=0, gravity=(0.0, 0.0, 0.0)) as sim:
+        sim.set_state(x, v, C, F.reshape(n, 3, 3))
+        s0 = sim.get_state()
+        sim.forward(40)
+        s1 = sim.get_state()
+    L0, scale = L(s0["x"], s0["v"], s0["C"])
+    L1, _ = L(s1["x"], s1["v"], s1["C"])
+    print("angular momentum", L0, L1, "scale", scale)
+    assert np.abs(L1 - L0).max() <= 1e-5 * scale, (L0, L1, scale)
+
+
 def test_one_step_parity_along_200_substep_trajectory():
     """Every substep of the 200-substep rollout (insert, then push at 10 m/s)
     against the oracle run for one substep from the GPU's own state: the
