@@ -537,11 +537,34 @@ def kernel_counters(name: str):
     return None
 
 
+def _code_only(text: str) -> str:
+    """C/CUDA source without comments, trailing blanks and empty lines: what
+    the compiler sees of it (comment edits leave the kernels, and so their
+    counters, unchanged)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = []
+    for line in text.splitlines():
+        cut = None
+        i = line.find("//")
+        while i >= 0:
+            if line.count('"', 0, i) % 2 == 0:   # not inside a string literal
+                cut = i
+                break
+            i = line.find("//", i + 2)
+        line = (line if cut is None else line[:cut]).rstrip()
+        if line:
+            out.append(line)
+    return "\n".join(out)
+
+
 def kernel_source_sha() -> str:
+    """Hash of the code (comments stripped) of the kernel sources the
+    particle kernels are built from."""
     import hashlib
     h = hashlib.sha256()
     for f in ("mpm_kernels.cu", "mpm_device.cuh", "mpm_types.h", "mpm_reg.h"):
-        h.update(open(os.path.join(ROOT, "paper_2510_17335_gb300", "csrc", f), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, "paper_2510_17335_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -7,13 +7,18 @@
 //               grid blocks. Particles whose F is ill-conditioned for FP32
 //               go to a list instead.
 //   k_p2g_fp64  the listed particles with the constitutive step in FP64
-//   k_grid      grid block (one warp): v = mv/m + dt g, walls, shovel contact
+//   k_grid      touched grid block (one warp): v = mv/m + dt g, walls,
+//               shovel contact
 //   k_g2p       particle: APIC gather of v and C, particle contact, advection
-// Adjoint substep (5 launches): k_g2p_bwd (scatter into the grid adjoint),
-// k_grid_bwd, k_p2g_bwd (gather, constitutive adjoint, parameter sums; the
-// same deferral), k_p2g_bwd_fp64, k_grid_clear.
+// Adjoint substep: k_g2p_bwd (scatter into the grid adjoint), k_grid_bwd,
+// k_p2g_bwd (gather, constitutive adjoint, parameter sums; the same
+// deferral), k_p2g_bwd_fp64, k_grid_clear. Inside a recorded segment the
+// P2G adjoint of substep k and the G2P adjoint of substep k-1 run as one
+// kernel (k_p2g_g2p_bwd + its FP64 fix-up), and k_grid_bwd clears the blocks
+// of the substep reversed before it, so a substep takes 4 launches.
+// The substep kernels use programmatic dependent launch (launch_pdl).
 //
-// The FP64 code lives only in the two fix-up kernels, so that the register
+// The FP64 code lives only in the fix-up kernels, so that the register
 // budget of the main particle kernels is set by the FP32 path.
 #include <cuda_runtime.h>
 
