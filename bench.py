@@ -33,17 +33,25 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "bed1m_grid128: 1,048,576 particles, 128^3 grid, skill-driven box shovel"
 
 # Algorithmic bytes per particle and launch: what the method must read and
-# write (FP32 state); the recorded SVD a recorded forward writes and the
-# adjoint reads back (96 B) is a compute-saving choice and shows in the
-# measured DRAM traffic, not here.
+# write with FP32 state (96 B per particle for x, v, C, F; the same for their
+# adjoints), plus the grid at 8 particles per cell with a 1.3x halo (about
+# 9 B per particle for a grid pass). A forward substep moves about 200 B per
+# particle (state read and written once, 192 B, and the grid); a backward
+# substep about 306 B (state k read, adjoint of k+1 read, adjoint of k
+# written: 288 B, and two grid-adjoint passes). The recorded SVD of the trial
+# F (written by a recorded forward, read by the adjoint) and the fused
+# kernels' savings (adjoints kept in registers between two substeps) are
+# implementation choices: they show in the measured DRAM traffic, not here.
+FWD_BYTES = 200          # per particle-substep, forward
+BWD_BYTES = 306          # per particle-substep, backward
 ALGO_BYTES = {
-    "k_p2g": 96 + 36,          # read x, v, C, F; write F
-    "k_g2p": 12 + 60,          # read x; write x, v, C
+    "k_p2g": 96 + 36,           # read x, v, C, F; write F
+    "k_g2p": 12 + 60,           # read x; write x, v, C
     "k_g2p_bwd": 12 + 60 + 12,  # read x, adj x/v/C; write adj x
     "k_p2g_bwd": 96 + 48 + 96,  # read state and adj x/F; write adj x/v/C/F
-    # fused P2G adjoint of substep k + G2P adjoint of k-1: read state k and
-    # adj x/F, write adj F and (partial) x, read x of state k-1
-    "k_p2g_g2p_bwd": 96 + 48 + 48 + 12,
+    # one launch reverses one substep's worth (the P2G adjoint of substep k
+    # and the G2P adjoint of k-1): the backward's bytes per particle-substep
+    "k_p2g_g2p_bwd": BWD_BYTES,
 }
 
 
@@ -487,6 +495,16 @@ def run_ours(args):
                    "issue_peak_per_s": ISSUE_PEAK, "issue_frac": round(ins / ISSUE_PEAK, 4),
                    "counts": "executed per launch (ncu, profiles/kernel_counters.txt)",
                    "peaks": "152 SMs x 128 FP32 lanes x 2 flop, 152 x 4 schedulers x 1 warp-instruction, at 2.07 GHz"}
+    # the whole step against the same peak: the method's bytes per
+    # particle-substep (forward + backward, and forward alone) over the
+    # measured step times
+    step_bytes = (FWD_BYTES + BWD_BYTES) * N * S
+    roof_step = {"bound": "hbm", "bytes_per_particle_substep": FWD_BYTES + BWD_BYTES,
+                 "achieved": round(step_bytes * args.steps / (ms / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                 "frac": round(step_bytes * args.steps / (ms / 1e3) / 1e9 / peak, 4),
+                 "fwd_bytes_per_particle_substep": FWD_BYTES,
+                 "fwd_frac": round(FWD_BYTES * N * S * args.steps / (fms / 1e3) / 1e9 / peak, 4),
+                 "peak_kind": f"{peak_kind} hbm_gbs"}
     batch = None
     if args.batch > 0:
         batch = batched_vs_serial(args.batch, args.batch_substeps, 3, args.sort)
@@ -507,7 +525,7 @@ def run_ours(args):
                    "l2": f"inputs larger than L2 (96 MB state, {record_bytes / 1e9:.1f} GB of recorded states and grids per step)",
                    "parallelism": f"replicas x{ws}"},
         "fwd_value": fwd_value, "fwd_ms_per_step": fms / args.steps,
-        "roofline": roof, "alu": alu, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "roofline": roof, "roofline_step": roof_step, "alu": alu, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "batched_vs_serial": batch,
         **({"sysid": sid} if sid is not None else {}),
         "kernels": kernels, "clocks": clk,
@@ -559,12 +577,17 @@ def _code_only(text: str) -> str:
 
 
 def kernel_source_sha() -> str:
-    """Hash of the code (comments stripped) of the kernel sources the
-    particle kernels are built from."""
+    """Hash of what the profiled kernels are built from: the code (comments
+    stripped) of their sources, including the launch constants, and the
+    nvcc architecture and flags."""
     import hashlib
+
+    from paper_2510_17335_gb300 import build
     h = hashlib.sha256()
-    for f in ("mpm_kernels.cu", "mpm_device.cuh", "mpm_types.h", "mpm_reg.h"):
+    for f in ("mpm_kernels.cu", "mpm_device.cuh", "mpm_types.h", "mpm_reg.h", "mpm_launch.h"):
         h.update(_code_only(open(os.path.join(ROOT, "paper_2510_17335_gb300", "csrc", f)).read()).encode())
+    flags = [f for f in build.FLAGS if not f.startswith("/") and ROOT not in f]
+    h.update(" ".join(build.ARCH + flags).encode())
     return h.hexdigest()[:16]
 
 

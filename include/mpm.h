@@ -320,8 +320,11 @@ const char* mpm_kernel_name(int kernel);
  * with MPM_ERR_INVALID_ARG before anything runs.
  *
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture. All calls share the one scratch array, which
+ * (cudaGetSymbolAddress, with that device current) and keeps it for that
+ * device's CUDA context; make that first call before any stream capture.
+ * After a device reset (cudaDeviceReset) the next call finds a new context
+ * and looks the address up again, so that call too should come before any
+ * capture. All calls share the one scratch array, which
  * keeps the last call's contents (the call clears the part that must start
  * at zero), so calls that overlap on the GPU race with each other: issue
  * them on one stream or one after another. */

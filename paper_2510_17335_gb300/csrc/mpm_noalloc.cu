@@ -7,6 +7,7 @@
 // implicit device synchronisation of an allocation. This entry point serves
 // them. Its only scratch is the file-scope device array below, of a fixed
 // size that every GPU loading the library holds until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -69,9 +70,48 @@ __global__ void __launch_bounds__(kThreads) k_loss_mse_noalloc(const float* __re
     }
 }
 
-// device address of g_loss_scratch, looked up once per device
+// Device address of g_loss_scratch per device, looked up once per CUDA
+// context: a device reset (cudaDeviceReset) destroys the context and the
+// module with it, and the array of the next context may sit elsewhere, so
+// the cache is keyed by the context's process-unique ID (cuCtxGetId, reached
+// through the runtime's driver entry points: no link to the driver library).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+struct ScratchCache {
+    bool valid = false;
+    unsigned long long ctx_id = 0;
+    LossScratch* addr = nullptr;
+};
+
 std::mutex g_mu;
-LossScratch* g_addr[64] = {nullptr};
+ScratchCache g_cache[64];
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+bool g_entry_points_tried = false;
+
+// ID of the current context (the primary context of the current device);
+// called with g_mu held
+int current_context_id(unsigned long long* id) {
+    if (!g_entry_points_tried) {
+        g_entry_points_tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    }
+    if (!g_ctx_get_current || !g_ctx_get_id) return MPM_ERR_CUDA;
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return MPM_ERR_NO_DEVICE;
+    if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return MPM_ERR_CUDA;
+    return MPM_OK;
+}
 
 int scratch_address(LossScratch** out) {
     int dev = 0;
@@ -79,16 +119,28 @@ int scratch_address(LossScratch** out) {
         cudaGetLastError();
         return MPM_ERR_NO_DEVICE;
     }
+    // makes the device's primary context current if nothing has yet (since
+    // CUDA 12 cudaSetDevice initialises the primary context)
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        cudaGetLastError();
+        return MPM_ERR_NO_DEVICE;
+    }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    unsigned long long id = 0;
+    const int rc = current_context_id(&id);
+    if (rc != MPM_OK) return rc;
+    ScratchCache& c = g_cache[dev];
+    if (!c.valid || c.ctx_id != id) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_loss_scratch) != cudaSuccess || p == nullptr) {
             cudaGetLastError();
             return MPM_ERR_CUDA;
         }
-        g_addr[dev] = static_cast<LossScratch*>(p);
+        c.addr = static_cast<LossScratch*>(p);
+        c.ctx_id = id;
+        c.valid = true;
     }
-    *out = g_addr[dev];
+    *out = c.addr;
     return MPM_OK;
 }
 

@@ -166,12 +166,32 @@ def _is_device(*arrays) -> bool:
 def loss_mse_noalloc(x, target, dL_dx=None, stream_ptr: int = 0) -> float:
     """mpm_loss_mse_noalloc on device tensors x, target [n, 3] (float32);
     writes dL/dx into dL_dx if given; returns the loss."""
+    import torch
+    # the C entry point reads and writes n * 3 floats of every array it is
+    # given: check the shapes and that all arrays live on one CUDA device
+    # before anything is launched
+    tensors = [("x", x), ("target", target)] + ([("dL_dx", dL_dx)] if dL_dx is not None else [])
+    for name, t in tensors:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"loss_mse_noalloc: {name} must be a torch tensor")
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"loss_mse_noalloc: {name} must be contiguous float32")
+    if x.dim() != 2 or x.shape[1] != 3:
+        raise ValueError(f"loss_mse_noalloc: x must be [n, 3], got {tuple(x.shape)}")
+    for name, t in tensors[1:]:
+        if t.shape != x.shape:
+            raise ValueError(f"loss_mse_noalloc: {name} has shape {tuple(t.shape)}, x has {tuple(x.shape)}")
+    if not all(t.is_cuda for _, t in tensors):
+        raise ValueError("loss_mse_noalloc: every array must be a CUDA tensor")
+    if len({t.device for _, t in tensors}) != 1:
+        raise ValueError("loss_mse_noalloc: every array must be on the same device")
     L = ctypes.c_double()
-    xp, _ = _ptr(x, True)
-    tp, _ = _ptr(target, True)
-    gp, _ = _ptr(dL_dx, True) if dL_dx is not None else (None, None)
-    check(lib().mpm_loss_mse_noalloc(xp, tp, int(x.shape[0]), gp, ctypes.byref(L), ctypes.c_void_p(stream_ptr)),
-          "mpm_loss_mse_noalloc")
+    with torch.cuda.device(x.device):
+        xp, _ = _ptr(x, True)
+        tp, _ = _ptr(target, True)
+        gp, _ = _ptr(dL_dx, True) if dL_dx is not None else (None, None)
+        check(lib().mpm_loss_mse_noalloc(xp, tp, int(x.shape[0]), gp, ctypes.byref(L),
+                                         ctypes.c_void_p(stream_ptr)), "mpm_loss_mse_noalloc")
     return L.value
 
 

@@ -88,3 +88,31 @@ def test_profile_kernel_table_matches_header(L):
     for k, name in re.findall(r"(\d+) (k_[a-z0-9_]+)", hdr):
         if int(k) < n:
             assert names[int(k)] == name, (k, name)
+
+
+def test_noalloc_wrapper_rejects_bad_arrays_before_launch(monkeypatch):
+    """The Python wrapper of mpm_loss_mse_noalloc checks shapes, dtypes and
+    devices before it reaches the library: a short target or gradient
+    buffer would otherwise be read or written past its end on the GPU."""
+    import torch
+
+    def no_lib():
+        raise AssertionError("the library must not be reached")
+
+    monkeypatch.setattr(mpm, "lib", no_lib)
+    x = torch.zeros((8, 3))
+    with pytest.raises(ValueError, match="target has shape"):
+        mpm.loss_mse_noalloc(x, torch.zeros((7, 3)))
+    with pytest.raises(ValueError, match="dL_dx has shape"):
+        mpm.loss_mse_noalloc(x, torch.zeros((8, 3)), torch.zeros((4, 3)))
+    with pytest.raises(ValueError, match=r"x must be \[n, 3\]"):
+        mpm.loss_mse_noalloc(torch.zeros((8, 2)), torch.zeros((8, 2)))
+    with pytest.raises(ValueError, match="x must be"):
+        mpm.loss_mse_noalloc(torch.zeros(24), torch.zeros(24))
+    with pytest.raises(ValueError, match="float32"):
+        mpm.loss_mse_noalloc(x.double(), torch.zeros((8, 3)))
+    with pytest.raises(TypeError):
+        mpm.loss_mse_noalloc(np.zeros((8, 3), np.float32), torch.zeros((8, 3)))
+    # right shapes, but host tensors: rejected as well
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        mpm.loss_mse_noalloc(x, torch.zeros((8, 3)), torch.zeros((8, 3)))
