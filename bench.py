@@ -167,12 +167,21 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle, as it stands, on a bounded sample
 # --------------------------------------------------------------------------
-def oracle_sample(w, cells: int, nsub: int, start_substep: int):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(w, cells: int, nsub: int, start_substep: int, threads: int = 1):
     """fwd+bwd of the oracle on the particles of a cells^3 block of the bed,
-    on the workload's own grid; returns (particle-substeps/s, seconds, description)."""
+    on the workload's own grid, with `threads` OpenMP threads (1: its plain
+    serial loops); returns (particle-substeps/s, seconds, description)."""
     import numpy as np
 
     import oracle
+    oracle.set_threads(threads)
 
     x0 = w.x0.astype(np.float64)
     lo = x0.min(0)
@@ -189,8 +198,9 @@ def oracle_sample(w, cells: int, nsub: int, start_substep: int):
     t0 = time.perf_counter()
     st, g = oracle.rollout_adjoint(p, x, v, C, F, poses, gx=gx)
     dt = time.perf_counter() - t0
-    desc = (f"oracle fwd+bwd (FP64 C, 1 thread): {n} particles ({cells}^3-cell block of the bed) x {nsub} substeps "
-            f"on the {w.res[0]}^3 grid")
+    oracle.set_threads(1)
+    desc = (f"oracle fwd+bwd (FP64 C, {threads} thread{'s' if threads > 1 else ''}): {n} particles ({cells}^3-cell "
+            f"block of the bed) x {nsub} substeps on the {w.res[0]}^3 grid")
     return n * nsub / dt, dt, desc
 
 
@@ -200,12 +210,13 @@ def run_reference(args):
         return
     from paper_2510_17335_gb300 import workloads as W
     w = W.cfg_1m()
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_sample(w, 16, 10, args.start)
+        oracle_sample(w, 16, 10, args.start, cores)
     rates, secs = [], 0.0
     desc = ""
     for _ in range(args.steps):
-        r, s, desc = oracle_sample(w, 16, 10, args.start)
+        r, s, desc = oracle_sample(w, 16, 10, args.start, cores)
         rates.append(r)
         secs += s
     value = sum(rates) / len(rates)
@@ -215,7 +226,7 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "substeps_per_step": args.substeps, "start_substep": args.start,
                        "sampled": "each step times the oracle on a bounded block of the bed (cpu_baseline.sample)"},
-            "cpu_baseline": {"value": value, "unit": "particle-substeps/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "particle-substeps/s", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "particle-substeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -511,9 +522,14 @@ def run_ours(args):
     sid = sysid_leg(args.sysid, args.sysid_substeps, args.sysid_iters) if args.sysid > 0 else None
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        r, secs, desc = oracle_sample(w, 24, 40, args.start)   # about 12 s on one core
-        cpu = {"value": r, "unit": "particle-substeps/s", "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": round(secs, 2)}
+        # the oracle on every host core (OpenMP), and its plain serial loops
+        # on one core (about 14 s), on the same bounded sample
+        cores = host_cores()
+        r, secs, desc = oracle_sample(w, 24, 40, args.start, cores)
+        r1, secs1, desc1 = oracle_sample(w, 24, 40, args.start, 1)
+        cpu = {"value": r, "unit": "particle-substeps/s", "cores": cores, "kind": "oracle", "sample": desc,
+               "seconds": round(secs, 2),
+               "single_thread": {"value": r1, "cores": 1, "seconds": round(secs1, 2), "sample": desc1}}
     line = {
         "metric": "particle-substeps/s (fwd+bwd)", "value": value, "unit": "particle-substeps/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
         stale = t < os.path.getmtime(_SRC) or t < os.path.getmtime(_HDR)
     if stale:
         tmp = _SO + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
                "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _SO)
@@ -151,6 +151,8 @@ class ObsGrid:
 def _declare(L):
     P = ctypes.POINTER(_Params)
     i64 = ctypes.c_int64
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_get_threads.restype = ctypes.c_int
     L.orc_svd3.argtypes = [_dp, _dp, _dp, _dp]
     L.orc_material.argtypes = [ctypes.c_double] * 3 + [_dp] * 3
     L.orc_constitutive.argtypes = [_dp] + [ctypes.c_double] * 4 + [_dp] * 3
@@ -309,6 +311,16 @@ def pose_table_adjoint(n_actions: int, substeps_per_action: int, dt_sub: float, 
     out = np.zeros((max(n_actions, 1), 6))
     _L().orc_pose_table_adjoint(n_actions, substeps_per_action, dt_sub, gposes.shape[0], _d(gposes), _d(out))
     return out[:n_actions]
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's particle and node loops (1: the plain serial
+    loops; more: OpenMP with per-thread grids, sums in thread order)."""
+    _L().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_L().orc_get_threads())
 
 
 def mse_loss(x, target) -> tuple[float, np.ndarray]:

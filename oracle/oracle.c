@@ -26,6 +26,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_EINVAL (-1)
@@ -508,45 +511,143 @@ static int64_t node_index(const orc_params* p, int i, int j, int k) {
     return ((int64_t)i * p->res[1] + j) * p->res[2] + k;
 }
 
+/* A box of grid nodes [o, o + d) per axis, stored row-major (x, y, z). The
+ * whole grid is the box with o = 0 and d = res, whose index is node_index. */
+typedef struct {
+    int o[3], d[3];
+} gview;
+
+static gview whole_grid(const orc_params* p) {
+    gview g = {{0, 0, 0}, {p->res[0], p->res[1], p->res[2]}};
+    return g;
+}
+
+static int64_t view_index(const gview* g, int i, int j, int k) {
+    return ((int64_t)(i - g->o[0]) * g->d[1] + (j - g->o[1])) * g->d[2] + (k - g->o[2]);
+}
+
+static int64_t view_size(const gview* g) { return (int64_t)g->d[0] * g->d[1] * g->d[2]; }
+
 static int in_domain(const orc_params* p, const double* xp) {
     for (int a = 0; a < 3; a++)
         if (!(xp[a] >= p->dx && xp[a] < (p->res[a] - 2) * p->dx)) return 0;
     return 1;
 }
 
-/* Particle part of Algorithm 1 before the grid: F trial, SVD,
- * constitutive, P2G. Writes F' into Fout and scatters into m, mv. */
+/* Particle part of Algorithm 1 for particle q: F trial, SVD, constitutive,
+ * P2G. Writes F' into Fout (if given) and scatters into m, mv (laid out as
+ * the box g). */
+static void p2g_one(const orc_params* p, double mu, double lam, double alpha, int64_t q, const double* x,
+                    const double* v, const double* C, const double* F, double* Fout, const gview* g, double* m,
+                    double* mv) {
+    double mp = p->rho * p->vol;
+    double inv_dx = 1.0 / p->dx;
+    const double* Cp = C + 9 * q;
+    double Ft[9], IC[9];
+    for (int i = 0; i < 9; i++) IC[i] = p->dt * Cp[i] + (i % 4 == 0 ? 1.0 : 0.0);
+    mm(IC, F + 9 * q, Ft);
+    double Fn[9], tau[9];
+    orc_constitutive(Ft, mu, lam, alpha, p->sigma_min, Fn, tau, NULL);
+    if (Fout) memcpy(Fout + 9 * q, Fn, sizeof Fn);
+    double A[9];
+    for (int i = 0; i < 9; i++) A[i] = -p->dt * p->vol * 4.0 * inv_dx * inv_dx * tau[i] + mp * Cp[i];
+    stencil s;
+    make_stencil(p, x + 3 * q, &s);
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            for (int c = 0; c < 3; c++) {
+                double W = s.w[0][a] * s.w[1][b] * s.w[2][c];
+                double d[3] = {(a - s.fx[0]) * p->dx, (b - s.fx[1]) * p->dx, (c - s.fx[2]) * p->dx};
+                int64_t id = view_index(g, s.base[0] + a, s.base[1] + b, s.base[2] + c);
+                m[id] += W * mp;
+                for (int k = 0; k < 3; k++) {
+                    double Ad = A[3 * k] * d[0] + A[3 * k + 1] * d[1] + A[3 * k + 2] * d[2];
+                    mv[3 * id + k] += W * (mp * v[3 * q + k] + Ad);
+                }
+            }
+}
+
+/* Threads of the OpenMP paths: 1 runs the plain loops, one particle or node
+ * at a time in index order. With more, particle loops are split across
+ * threads; scatters go into per-thread grids over the box of the particles'
+ * stencils, which are then added node by node in thread order, and scalar
+ * sums are per-thread partials added in thread order: the same arithmetic
+ * as one thread up to the order of the sums. */
+static int orc_threads = 1;
+
+void orc_set_threads(int n) { orc_threads = n < 1 ? 1 : n; }
+
+int orc_get_threads(void) { return orc_threads; }
+
+/* the box of nodes that the stencils of particles x[0..n) touch */
+static gview stencil_box(const orc_params* p, int64_t n, const double* x) {
+    int lo[3] = {p->res[0], p->res[1], p->res[2]}, hi[3] = {-1, -1, -1};
+    for (int64_t q = 0; q < n; q++) {
+        stencil s;
+        make_stencil(p, x + 3 * q, &s);
+        for (int a = 0; a < 3; a++) {
+            if (s.base[a] < lo[a]) lo[a] = s.base[a];
+            if (s.base[a] + 2 > hi[a]) hi[a] = s.base[a] + 2;
+        }
+    }
+    gview g;
+    for (int a = 0; a < 3; a++) {
+        g.o[a] = n > 0 ? lo[a] : 0;
+        g.d[a] = n > 0 ? hi[a] - lo[a] + 1 : 0;
+    }
+    return g;
+}
+
+/* adds the per-thread box grids part[t] (ncomp values per node) into the
+ * whole grid dst, in thread order per node */
+static void add_box_partials(const orc_params* p, const gview* g, int T, const double* part, int ncomp, double* dst) {
+    const int64_t nb = view_size(g);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
+#endif
+    for (int64_t b = 0; b < nb; b++) {
+        const int iz = g->o[2] + (int)(b % g->d[2]);
+        const int iy = g->o[1] + (int)((b / g->d[2]) % g->d[1]);
+        const int ix = g->o[0] + (int)(b / ((int64_t)g->d[1] * g->d[2]));
+        const int64_t id = node_index(p, ix, iy, iz);
+        for (int t = 0; t < T; t++)
+            for (int c = 0; c < ncomp; c++) dst[ncomp * id + c] += part[((int64_t)t * nb + b) * ncomp + c];
+    }
+}
+
+/* Particle part of Algorithm 1 before the grid, for every particle: F
+ * trial, SVD, constitutive, P2G. Writes F' into Fout and scatters into m,
+ * mv (the whole grid, which the caller has zeroed). */
 static void particle_to_grid(const orc_params* p, int64_t n, const double* x, const double* v,
                              const double* C, const double* F, double* Fout, double* m, double* mv) {
     double mu, lam, alpha;
     orc_material(p->E, p->nu, p->phi_deg, &mu, &lam, &alpha);
-    double mp = p->rho * p->vol;
-    double inv_dx = 1.0 / p->dx;
-    for (int64_t q = 0; q < n; q++) {
-        const double* Cp = C + 9 * q;
-        double Ft[9], IC[9];
-        for (int i = 0; i < 9; i++) IC[i] = p->dt * Cp[i] + (i % 4 == 0 ? 1.0 : 0.0);
-        mm(IC, F + 9 * q, Ft);
-        double Fn[9], tau[9];
-        orc_constitutive(Ft, mu, lam, alpha, p->sigma_min, Fn, tau, NULL);
-        if (Fout) memcpy(Fout + 9 * q, Fn, sizeof Fn);
-        double A[9];
-        for (int i = 0; i < 9; i++) A[i] = -p->dt * p->vol * 4.0 * inv_dx * inv_dx * tau[i] + mp * Cp[i];
-        stencil s;
-        make_stencil(p, x + 3 * q, &s);
-        for (int a = 0; a < 3; a++)
-            for (int b = 0; b < 3; b++)
-                for (int c = 0; c < 3; c++) {
-                    double W = s.w[0][a] * s.w[1][b] * s.w[2][c];
-                    double d[3] = {(a - s.fx[0]) * p->dx, (b - s.fx[1]) * p->dx, (c - s.fx[2]) * p->dx};
-                    int64_t id = node_index(p, s.base[0] + a, s.base[1] + b, s.base[2] + c);
-                    m[id] += W * mp;
-                    for (int k = 0; k < 3; k++) {
-                        double Ad = A[3 * k] * d[0] + A[3 * k + 1] * d[1] + A[3 * k + 2] * d[2];
-                        mv[3 * id + k] += W * (mp * v[3 * q + k] + Ad);
-                    }
-                }
+    if (orc_threads <= 1) {
+        const gview g = whole_grid(p);
+        for (int64_t q = 0; q < n; q++) p2g_one(p, mu, lam, alpha, q, x, v, C, F, Fout, &g, m, mv);
+        return;
     }
+    const gview g = stencil_box(p, n, x);
+    const int T = orc_threads;
+    const int64_t nb = view_size(&g);
+    double* pm = calloc((size_t)T * nb, sizeof(double));
+    double* pmv = calloc((size_t)T * nb * 3, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(T)
+#endif
+    {
+#ifdef _OPENMP
+        const int t = omp_get_thread_num();
+#pragma omp for schedule(static)
+#else
+        const int t = 0;
+#endif
+        for (int64_t q = 0; q < n; q++) p2g_one(p, mu, lam, alpha, q, x, v, C, F, Fout, &g, pm + t * nb, pmv + 3 * t * nb);
+    }
+    add_box_partials(p, &g, T, pm, 1, m);
+    add_box_partials(p, &g, T, pmv, 3, mv);
+    free(pm);
+    free(pmv);
 }
 
 /* Grid part of Algorithm 1: gravity, walls, shovel contact at one node. */
@@ -565,6 +666,10 @@ static void grid_node_update(const orc_params* p, int i, int j, int k, double m,
 
 static void grid_update(const orc_params* p, const double* m, const double* mv, const double pose[8],
                         double* vout) {
+    /* nodes are independent: threads give the same values */
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(orc_threads) schedule(static) if (orc_threads > 1)
+#endif
     for (int i = 0; i < p->res[0]; i++)
         for (int j = 0; j < p->res[1]; j++)
             for (int k = 0; k < p->res[2]; k++) {
@@ -638,8 +743,12 @@ int orc_substep(const orc_params* p, int64_t n, double* x, double* v, double* C,
     particle_to_grid(p, n, x, v, C, F, F, m, mv);
     /* move agent: the pose of this substep is given; grid update */
     grid_update(p, m, mv, pose, vo);
-    /* particle loop: G2P, particle collision, advection */
+    /* particle loop: G2P, particle collision, advection (particles are
+     * independent: threads give the same values) */
     int status = ORC_OK;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(orc_threads) schedule(static) if (orc_threads > 1) reduction(min : status)
+#endif
     for (int64_t q = 0; q < n; q++) {
         double vnew[3], Cnew[9], vpost[3];
         g2p_one(p, x + 3 * q, vo, vnew, Cnew);
@@ -704,6 +813,144 @@ void orc_grad_op(const orc_params* p, double* g, int64_t n) {
     }
 }
 
+/* Reverse of advection, particle collision and G2P for particle q of the
+ * state x: reads its adjoints ax, av (already regularised) and aC, scatters
+ * the grid-velocity adjoint into avo (laid out as the box g), adds to the
+ * pose adjoint gpose and leaves the partial adjoint of x in ax. */
+static void g2p_adjoint_one(const orc_params* p, int64_t q, const double* x, const double* vo, const double pose[8],
+                            const gview* g, double* ax, const double* av, const double* aC, double* avo,
+                            double gpose[8]) {
+    double inv_dx = 1.0 / p->dx, kap = 4.0 * inv_dx * inv_dx;
+    const double* xp = x + 3 * q;
+    double gxp[3] = {ax[3 * q], ax[3 * q + 1], ax[3 * q + 2]};
+    double gvpost[3];
+    for (int k = 0; k < 3; k++) gvpost[k] = av[3 * q + k] + p->dt * ax[3 * q + k];
+    double vnew[3], Cnew[9];
+    g2p_one(p, xp, vo, vnew, Cnew);
+    double gvnew[3] = {0, 0, 0};
+    if (p->particle_collision)
+        shovel_project_adjoint(p, vnew, xp, pose, gvpost, gvnew, gxp, gpose);
+    else
+        for (int k = 0; k < 3; k++) gvnew[k] = gvpost[k];
+    const double* gCn = aC + 9 * q;
+    stencil st;
+    make_stencil(p, xp, &st);
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            for (int c = 0; c < 3; c++) {
+                int o[3] = {a, b, c};
+                double wv[3] = {st.w[0][a], st.w[1][b], st.w[2][c]};
+                double dwv[3] = {st.dw[0][a], st.dw[1][b], st.dw[2][c]};
+                double W = wv[0] * wv[1] * wv[2];
+                double gradW[3] = {dwv[0] * wv[1] * wv[2], wv[0] * dwv[1] * wv[2], wv[0] * wv[1] * dwv[2]};
+                double d[3];
+                for (int k = 0; k < 3; k++) d[k] = (o[k] - st.fx[k]) * p->dx;
+                const double* vi = vo + 3 * node_index(p, st.base[0] + a, st.base[1] + b, st.base[2] + c);
+                int64_t id = view_index(g, st.base[0] + a, st.base[1] + b, st.base[2] + c);
+                double Wbar = 0, dbar[3] = {0, 0, 0};
+                for (int r = 0; r < 3; r++) {
+                    double Cd = gCn[3 * r] * d[0] + gCn[3 * r + 1] * d[1] + gCn[3 * r + 2] * d[2];
+                    avo[3 * id + r] += W * gvnew[r] + kap * W * Cd;
+                    Wbar += vi[r] * gvnew[r] + kap * vi[r] * Cd;
+                    for (int k = 0; k < 3; k++) dbar[k] += kap * W * gCn[3 * r + k] * vi[r];
+                }
+                for (int k = 0; k < 3; k++) gxp[k] += Wbar * gradW[k] - dbar[k];
+            }
+    for (int k = 0; k < 3; k++) ax[3 * q + k] = gxp[k];
+}
+
+/* Reverse of the grid update for the nodes of slab x = i: from the
+ * adjoint of the velocity after the contact (avo) to that of the momentum
+ * before the division by the mass (amv, walls applied); adds to gpose. */
+static void grid_adjoint_slab(const orc_params* p, int i, const double* m, const double* mv, const double pose[8],
+                              const double* avo, double* amv, double gpose[8]) {
+    for (int j = 0; j < p->res[1]; j++)
+        for (int k = 0; k < p->res[2]; k++) {
+            int64_t id = node_index(p, i, j, k);
+            if (!(m[id] > 0)) continue;
+            int idx[3] = {i, j, k};
+            double vg[3], mask[3] = {1, 1, 1};
+            for (int a = 0; a < 3; a++) vg[a] = mv[3 * id + a] / m[id] + p->dt * p->gravity[a];
+            for (int a = 0; a < 3; a++) {
+                if (idx[a] < p->bound && vg[a] < 0) { vg[a] = 0; mask[a] = 0; }
+                if (idx[a] > p->res[a] - p->bound && vg[a] > 0) { vg[a] = 0; mask[a] = 0; }
+            }
+            double q[3] = {i * p->dx, j * p->dx, k * p->dx}, gq[3] = {0, 0, 0};
+            double gvg[3] = {0, 0, 0};
+            shovel_project_adjoint(p, vg, q, pose, avo + 3 * id, gvg, gq, gpose);
+            for (int a = 0; a < 3; a++) amv[3 * id + a] = gvg[a] * mask[a];   /* v-bar before the contact */
+        }
+}
+
+/* Reverse of P2G and of the constitutive step for particle q of the
+ * state (x, v, C, F) with Kirchhoff stress tau: gathers the grid adjoints
+ * am, amv; turns the adjoints of particle q (ax partial, aF) into those of
+ * the state before the substep (ax, av, aC, aF) and adds to the sums of
+ * dL/dmu, dL/dlambda, dL/dalpha and dL/dm_p. */
+static void p2g_adjoint_one(const orc_params* p, double mu, double lam, double alpha, int64_t q, const double* x,
+                            const double* v, const double* C, const double* F, const double* tau, const double* am,
+                            const double* amv, double* ax, double* av, double* aC, double* aF, double* gmu_acc,
+                            double* glam_acc, double* galpha_acc, double* gmp_acc) {
+    double mp = p->rho * p->vol;
+    double inv_dx = 1.0 / p->dx, kap = 4.0 * inv_dx * inv_dx;
+    const double* xp = x + 3 * q;
+    const double* Cp = C + 9 * q;
+    const double* vp = v + 3 * q;
+    double A[9];
+    for (int i = 0; i < 9; i++) A[i] = -p->dt * p->vol * kap * tau[9 * q + i] + mp * Cp[i];
+    double gxp[3] = {ax[3 * q], ax[3 * q + 1], ax[3 * q + 2]};
+    double gvp[3] = {0, 0, 0}, gA[9] = {0}, gmpp = 0;
+    stencil st;
+    make_stencil(p, xp, &st);
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            for (int c = 0; c < 3; c++) {
+                int o[3] = {a, b, c};
+                double wv[3] = {st.w[0][a], st.w[1][b], st.w[2][c]};
+                double dwv[3] = {st.dw[0][a], st.dw[1][b], st.dw[2][c]};
+                double W = wv[0] * wv[1] * wv[2];
+                double gradW[3] = {dwv[0] * wv[1] * wv[2], wv[0] * dwv[1] * wv[2], wv[0] * wv[1] * dwv[2]};
+                double d[3];
+                for (int k = 0; k < 3; k++) d[k] = (o[k] - st.fx[k]) * p->dx;
+                int64_t id = node_index(p, st.base[0] + a, st.base[1] + b, st.base[2] + c);
+                const double* gmv = amv + 3 * id;
+                double Wbar = am[id] * mp;
+                double dbar[3] = {0, 0, 0};
+                for (int r = 0; r < 3; r++) {
+                    double Ad = A[3 * r] * d[0] + A[3 * r + 1] * d[1] + A[3 * r + 2] * d[2];
+                    Wbar += gmv[r] * (mp * vp[r] + Ad);
+                    gvp[r] += W * mp * gmv[r];
+                    gmpp += W * gmv[r] * vp[r];
+                    for (int k = 0; k < 3; k++) {
+                        gA[3 * r + k] += W * gmv[r] * d[k];
+                        dbar[k] += W * A[3 * r + k] * gmv[r];
+                    }
+                }
+                gmpp += W * am[id];
+                for (int k = 0; k < 3; k++) gxp[k] += Wbar * gradW[k] - dbar[k];
+            }
+    double gtau[9], gCp[9];
+    for (int i = 0; i < 9; i++) {
+        gtau[i] = -p->dt * p->vol * kap * gA[i];
+        gCp[i] = mp * gA[i];
+        gmpp += gA[i] * Cp[i];
+    }
+    double Ft[9], IC[9], gFt[9];
+    for (int i = 0; i < 9; i++) IC[i] = p->dt * Cp[i] + (i % 4 == 0 ? 1.0 : 0.0);
+    mm(IC, F + 9 * q, Ft);
+    orc_constitutive_adjoint(Ft, mu, lam, alpha, p->sigma_min, aF + 9 * q, gtau, gFt, gmu_acc, glam_acc, galpha_acc);
+    /* Ft = (I + dt C) F */
+    double gFp[9], t2[9];
+    mtm(IC, gFt, gFp);
+    mmt(gFt, F + 9 * q, t2);
+    for (int i = 0; i < 9; i++) gCp[i] += p->dt * t2[i];
+    memcpy(ax + 3 * q, gxp, sizeof gxp);
+    memcpy(av + 3 * q, gvp, sizeof gvp);
+    memcpy(aC + 9 * q, gCp, sizeof gCp);
+    memcpy(aF + 9 * q, gFp, sizeof gFp);
+    *gmp_acc += gmpp;
+}
+
 int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const double* v0,
                         const double* C0, const double* F0, int nsub, const double* poses,
                         const double* gx, const double* gv, const double* gC, const double* gF,
@@ -712,8 +959,6 @@ int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const 
     if (!check_params(p) || nsub < 0) return ORC_EINVAL;
     double mu, lam, alpha;
     orc_material(p->E, p->nu, p->phi_deg, &mu, &lam, &alpha);
-    double mp = p->rho * p->vol;
-    double inv_dx = 1.0 / p->dx, kap = 4.0 * inv_dx * inv_dx;
     int64_t G = grid_size(p);
     /* tape of the states at the start of every substep */
     double* tx = malloc((size_t)(nsub + 1) * n * 3 * sizeof(double));
@@ -767,6 +1012,9 @@ int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const 
         memset(mv, 0, 3 * G * sizeof(double));
         particle_to_grid(p, n, x, v, C, F, NULL, m, mv);
         grid_update(p, m, mv, pose, vo);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(orc_threads) schedule(static) if (orc_threads > 1)
+#endif
         for (int64_t q = 0; q < n; q++) {
             double Ft[9], IC[9], Fn[9];
             for (int i = 0; i < 9; i++) IC[i] = p->dt * C[9 * q + i] + (i % 4 == 0 ? 1.0 : 0.0);
@@ -781,43 +1029,33 @@ int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const 
         /* reverse of advection, particle collision and G2P; the partial
          * adjoint of x is kept in ax, the grid velocity adjoint goes to avo */
         memset(avo, 0, 3 * G * sizeof(double));
-        for (int64_t q = 0; q < n; q++) {
-            const double* xp = x + 3 * q;
-            double gxp[3] = {ax[3 * q], ax[3 * q + 1], ax[3 * q + 2]};
-            double gvpost[3];
-            for (int k = 0; k < 3; k++) gvpost[k] = av[3 * q + k] + p->dt * ax[3 * q + k];
-            double vnew[3], Cnew[9];
-            g2p_one(p, xp, vo, vnew, Cnew);
-            double gvnew[3] = {0, 0, 0};
-            if (p->particle_collision)
-                shovel_project_adjoint(p, vnew, xp, pose, gvpost, gvnew, gxp, gpose);
-            else
-                for (int k = 0; k < 3; k++) gvnew[k] = gvpost[k];
-            const double* gCn = aC + 9 * q;
-            stencil st;
-            make_stencil(p, xp, &st);
-            for (int a = 0; a < 3; a++)
-                for (int b = 0; b < 3; b++)
-                    for (int c = 0; c < 3; c++) {
-                        int o[3] = {a, b, c};
-                        double wv[3] = {st.w[0][a], st.w[1][b], st.w[2][c]};
-                        double dwv[3] = {st.dw[0][a], st.dw[1][b], st.dw[2][c]};
-                        double W = wv[0] * wv[1] * wv[2];
-                        double gradW[3] = {dwv[0] * wv[1] * wv[2], wv[0] * dwv[1] * wv[2], wv[0] * wv[1] * dwv[2]};
-                        double d[3];
-                        for (int k = 0; k < 3; k++) d[k] = (o[k] - st.fx[k]) * p->dx;
-                        int64_t id = node_index(p, st.base[0] + a, st.base[1] + b, st.base[2] + c);
-                        const double* vi = vo + 3 * id;
-                        double Wbar = 0, dbar[3] = {0, 0, 0};
-                        for (int r = 0; r < 3; r++) {
-                            double Cd = gCn[3 * r] * d[0] + gCn[3 * r + 1] * d[1] + gCn[3 * r + 2] * d[2];
-                            avo[3 * id + r] += W * gvnew[r] + kap * W * Cd;
-                            Wbar += vi[r] * gvnew[r] + kap * vi[r] * Cd;
-                            for (int k = 0; k < 3; k++) dbar[k] += kap * W * gCn[3 * r + k] * vi[r];
-                        }
-                        for (int k = 0; k < 3; k++) gxp[k] += Wbar * gradW[k] - dbar[k];
-                    }
-            for (int k = 0; k < 3; k++) ax[3 * q + k] = gxp[k];
+        if (orc_threads <= 1) {
+            const gview g = whole_grid(p);
+            for (int64_t q = 0; q < n; q++) g2p_adjoint_one(p, q, x, vo, pose, &g, ax, av, aC, avo, gpose);
+        } else {
+            const gview g = stencil_box(p, n, x);
+            const int T = orc_threads;
+            const int64_t nb = view_size(&g);
+            double* pavo = calloc((size_t)T * nb * 3, sizeof(double));
+            double* pgp = calloc((size_t)T * 8, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(T)
+#endif
+            {
+#ifdef _OPENMP
+                const int t = omp_get_thread_num();
+#pragma omp for schedule(static)
+#else
+                const int t = 0;
+#endif
+                for (int64_t q = 0; q < n; q++)
+                    g2p_adjoint_one(p, q, x, vo, pose, &g, ax, av, aC, pavo + 3 * t * nb, pgp + 8 * t);
+            }
+            add_box_partials(p, &g, T, pavo, 3, avo);
+            for (int t = 0; t < T; t++)
+                for (int k = 0; k < 8; k++) gpose[k] += pgp[8 * t + k];
+            free(pavo);
+            free(pgp);
         }
         /* reverse of the grid update: the adjoint of the velocity after the
          * contact (regularised), then of the velocity before it (for every
@@ -825,24 +1063,31 @@ int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const 
         orc_grad_op(p, avo, 3 * G);
         memset(am, 0, G * sizeof(double));
         memset(amv, 0, 3 * G * sizeof(double));
-        for (int i = 0; i < p->res[0]; i++)
-            for (int j = 0; j < p->res[1]; j++)
-                for (int k = 0; k < p->res[2]; k++) {
-                    int64_t id = node_index(p, i, j, k);
-                    if (!(m[id] > 0)) continue;
-                    int idx[3] = {i, j, k};
-                    double vg[3], mask[3] = {1, 1, 1};
-                    for (int a = 0; a < 3; a++) vg[a] = mv[3 * id + a] / m[id] + p->dt * p->gravity[a];
-                    for (int a = 0; a < 3; a++) {
-                        if (idx[a] < p->bound && vg[a] < 0) { vg[a] = 0; mask[a] = 0; }
-                        if (idx[a] > p->res[a] - p->bound && vg[a] > 0) { vg[a] = 0; mask[a] = 0; }
-                    }
-                    double q[3] = {i * p->dx, j * p->dx, k * p->dx}, gq[3] = {0, 0, 0};
-                    double gvg[3] = {0, 0, 0};
-                    shovel_project_adjoint(p, vg, q, pose, avo + 3 * id, gvg, gq, gpose);
-                    for (int a = 0; a < 3; a++) amv[3 * id + a] = gvg[a] * mask[a];   /* v-bar before the contact */
-                }
+        if (orc_threads <= 1) {
+            for (int i = 0; i < p->res[0]; i++) grid_adjoint_slab(p, i, m, mv, pose, avo, amv, gpose);
+        } else {
+            const int T = orc_threads;
+            double* pgp = calloc((size_t)T * 8, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(T)
+#endif
+            {
+#ifdef _OPENMP
+                const int t = omp_get_thread_num();
+#pragma omp for schedule(static)
+#else
+                const int t = 0;
+#endif
+                for (int i = 0; i < p->res[0]; i++) grid_adjoint_slab(p, i, m, mv, pose, avo, amv, pgp + 8 * t);
+            }
+            for (int t = 0; t < T; t++)
+                for (int k = 0; k < 8; k++) gpose[k] += pgp[8 * t + k];
+            free(pgp);
+        }
         orc_grad_op(p, amv, 3 * G);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(orc_threads) schedule(static) if (orc_threads > 1)
+#endif
         for (int64_t id = 0; id < G; id++) {
             if (!(m[id] > 0)) continue;
             double dot = 0;
@@ -854,64 +1099,34 @@ int orc_rollout_adjoint(const orc_params* p, int64_t n, const double* x0, const 
         }
         orc_grad_op(p, am, G);
         /* reverse of P2G and the constitutive step */
-        for (int64_t q = 0; q < n; q++) {
-            const double* xp = x + 3 * q;
-            const double* Cp = C + 9 * q;
-            const double* vp = v + 3 * q;
-            double A[9];
-            for (int i = 0; i < 9; i++) A[i] = -p->dt * p->vol * kap * tau[9 * q + i] + mp * Cp[i];
-            double gxp[3] = {ax[3 * q], ax[3 * q + 1], ax[3 * q + 2]};
-            double gvp[3] = {0, 0, 0}, gA[9] = {0}, gmpp = 0;
-            stencil st;
-            make_stencil(p, xp, &st);
-            for (int a = 0; a < 3; a++)
-                for (int b = 0; b < 3; b++)
-                    for (int c = 0; c < 3; c++) {
-                        int o[3] = {a, b, c};
-                        double wv[3] = {st.w[0][a], st.w[1][b], st.w[2][c]};
-                        double dwv[3] = {st.dw[0][a], st.dw[1][b], st.dw[2][c]};
-                        double W = wv[0] * wv[1] * wv[2];
-                        double gradW[3] = {dwv[0] * wv[1] * wv[2], wv[0] * dwv[1] * wv[2], wv[0] * wv[1] * dwv[2]};
-                        double d[3];
-                        for (int k = 0; k < 3; k++) d[k] = (o[k] - st.fx[k]) * p->dx;
-                        int64_t id = node_index(p, st.base[0] + a, st.base[1] + b, st.base[2] + c);
-                        const double* gmv = amv + 3 * id;
-                        double Wbar = am[id] * mp;
-                        double dbar[3] = {0, 0, 0};
-                        for (int r = 0; r < 3; r++) {
-                            double Ad = A[3 * r] * d[0] + A[3 * r + 1] * d[1] + A[3 * r + 2] * d[2];
-                            Wbar += gmv[r] * (mp * vp[r] + Ad);
-                            gvp[r] += W * mp * gmv[r];
-                            gmpp += W * gmv[r] * vp[r];
-                            for (int k = 0; k < 3; k++) {
-                                gA[3 * r + k] += W * gmv[r] * d[k];
-                                dbar[k] += W * A[3 * r + k] * gmv[r];
-                            }
-                        }
-                        gmpp += W * am[id];
-                        for (int k = 0; k < 3; k++) gxp[k] += Wbar * gradW[k] - dbar[k];
-                    }
-            double gtau[9], gCp[9];
-            for (int i = 0; i < 9; i++) {
-                gtau[i] = -p->dt * p->vol * kap * gA[i];
-                gCp[i] = mp * gA[i];
-                gmpp += gA[i] * Cp[i];
+        if (orc_threads <= 1) {
+            for (int64_t q = 0; q < n; q++)
+                p2g_adjoint_one(p, mu, lam, alpha, q, x, v, C, F, tau, am, amv, ax, av, aC, aF, &gmu, &glam, &galpha,
+                                &gmp);
+        } else {
+            const int T = orc_threads;
+            double* part = calloc((size_t)T * 4, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(T)
+#endif
+            {
+#ifdef _OPENMP
+                const int t = omp_get_thread_num();
+#pragma omp for schedule(static)
+#else
+                const int t = 0;
+#endif
+                for (int64_t q = 0; q < n; q++)
+                    p2g_adjoint_one(p, mu, lam, alpha, q, x, v, C, F, tau, am, amv, ax, av, aC, aF, part + 4 * t,
+                                    part + 4 * t + 1, part + 4 * t + 2, part + 4 * t + 3);
             }
-            double Ft[9], IC[9], gFt[9];
-            for (int i = 0; i < 9; i++) IC[i] = p->dt * Cp[i] + (i % 4 == 0 ? 1.0 : 0.0);
-            mm(IC, F + 9 * q, Ft);
-            orc_constitutive_adjoint(Ft, mu, lam, alpha, p->sigma_min, aF + 9 * q, gtau, gFt, &gmu, &glam,
-                                     &galpha);
-            /* Ft = (I + dt C) F */
-            double gFp[9], t2[9];
-            mtm(IC, gFt, gFp);
-            mmt(gFt, F + 9 * q, t2);
-            for (int i = 0; i < 9; i++) gCp[i] += p->dt * t2[i];
-            memcpy(ax + 3 * q, gxp, sizeof gxp);
-            memcpy(av + 3 * q, gvp, sizeof gvp);
-            memcpy(aC + 9 * q, gCp, sizeof gCp);
-            memcpy(aF + 9 * q, gFp, sizeof gFp);
-            gmp += gmpp;
+            for (int t = 0; t < T; t++) {
+                gmu += part[4 * t];
+                glam += part[4 * t + 1];
+                galpha += part[4 * t + 2];
+                gmp += part[4 * t + 3];
+            }
+            free(part);
         }
         if (gposes) memcpy(gposes + 8 * s, gpose, sizeof gpose);
     }

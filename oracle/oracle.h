@@ -48,6 +48,14 @@ typedef struct {
  * each entry to [-clip_value, clip_value] instead. */
 void orc_grad_op(const orc_params* p, double* g, int64_t n);
 
+/* Threads of the particle and node loops (default 1: the plain loops, one
+ * particle or node at a time in index order). With n > 1 (OpenMP) scatters
+ * go into per-thread grids over the box of the particles' stencils, added
+ * node by node in thread order, and parameter sums are per-thread partials
+ * added in thread order: the same arithmetic up to the order of the sums. */
+void orc_set_threads(int n);
+int orc_get_threads(void);
+
 /* 3x3 SVD with proper rotations U, V (det +1) and S sorted by magnitude,
  * S[2] carrying the sign of det(F). */
 void orc_svd3(const double F[9], double U[9], double S[3], double V[9]);

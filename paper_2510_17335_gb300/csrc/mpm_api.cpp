@@ -190,7 +190,7 @@ struct mpm_handle {
     int tile_scatter = 1;
     // particle sort by grid block
     DevBuf<float> d_state2, d_adj2;
-    DevBuf<int> d_ext2, d_key, d_rank, d_bcount, d_bscan, d_part, d_perm, d_ext_rec;
+    DevBuf<int> d_ext2, d_key, d_rank, d_bcount, d_bscan, d_part, d_remap, d_perm, d_ext_rec;
     std::vector<DevBuf<int>> seg_perm;
     std::vector<char> seg_sorted;
     int64_t since_sort = 1LL << 40;
@@ -626,9 +626,10 @@ int sort_particles(mpm_handle* h, int* perm) {
     RK(h->d_bcount.ensure((size_t)n_keys, h->device_bytes));
     RK(h->d_bscan.ensure((size_t)n_keys, h->device_bytes));
     RK(h->d_part.ensure((size_t)(n_keys + 1023) / 1024, h->device_bytes));
+    RK(h->d_remap.ensure((size_t)std::max<int64_t>(h->n_ext, 1), h->device_bytes));
     CK(launch_sort(h->d_inst.p, h->d_chunk_inst.p, h->n_chunks, h->ncap, n_keys, h->d_state.p, h->d_state2.p,
                    h->d_ext_of_slot.p, h->d_ext2.p, h->d_key.p, h->d_rank.p, h->d_bcount.p, h->d_bscan.p, h->d_part.p,
-                   perm, h->stream));
+                   h->d_remap.p, perm, h->stream));
     h->launches += kSortLaunches;
     std::swap(h->d_state, h->d_state2);
     std::swap(h->d_ext_of_slot, h->d_ext2);
@@ -807,7 +808,8 @@ void mpm_destroy(mpm_handle* h) {
     h->d_adj.release(); h->d_gmat.release(); h->d_gpose.release();
     h->d_pstat.release(); h->d_gstat.release(); h->d_gpose_raw.release();
     h->d_state2.release(); h->d_adj2.release(); h->d_ext2.release(); h->d_key.release(); h->d_rank.release();
-    h->d_bcount.release(); h->d_bscan.release(); h->d_part.release(); h->d_perm.release(); h->d_ext_rec.release();
+    h->d_bcount.release(); h->d_bscan.release(); h->d_part.release(); h->d_remap.release(); h->d_perm.release();
+    h->d_ext_rec.release();
     for (auto& b : h->seg_perm) b.release();
     h->prof.release();
     if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);

@@ -1419,14 +1419,49 @@ __global__ void k_scan_add(int* out, const int* part, int n) {
     if (i < n) out[i] += part[i / 1024];
 }
 
+// Order inside a grid block: the cell-major order of the counting sort
+// (cell_start + rank) is rearranged rank-major: first the rank-0 particle of
+// every occupied cell of the block (cells in block order), then the rank-1
+// particles, and so on. A warp then holds particles of up to 32 different
+// cells, so the 32 lanes of a scatter instruction never add to one node, and
+// a CTA's 256 particles still lie in one or two neighbouring blocks.
+// remap[cell_start + rank] = the particle's position in that order (in the
+// same numbering as cell_start). One 64-thread CTA (a thread per cell) per
+// grid block.
+__global__ void __launch_bounds__(64) k_sort_interleave(const int* bcount, const int* bscan, int* remap) {
+    __shared__ int wtot[2], wmax[2];
+    const int b = blockIdx.x, c = threadIdx.x, lane = c & 31, w = c >> 5;
+    const int cnt = bcount[b * 64 + c];
+    int m = cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) wmax[w] = m;
+    __syncthreads();
+    const int rmax = max(wmax[0], wmax[1]);
+    if (rmax == 0) return;   // empty block (uniform)
+    const int start = bscan[b * 64 + c];
+    const int bstart = bscan[b * 64];
+    int base = 0;
+    for (int r = 0; r < rmax; r++) {
+        const bool has = cnt > r;
+        const unsigned bal = __ballot_sync(0xffffffffu, has);
+        __syncthreads();   // wtot of the previous round has been read
+        if (lane == 0) wtot[w] = __popc(bal);
+        __syncthreads();
+        const int off = __popc(bal & ((1u << lane) - 1u)) + (w == 1 ? wtot[0] : 0);
+        if (has) remap[start + r] = bstart + base + off;
+        base += wtot[0] + wtot[1];
+    }
+}
+
 // new slot of every particle; perm[new] = old, ext carried along
 __global__ void __launch_bounds__(kChunk) k_sort_perm(const InstDev* inst, const int* chunk_inst, const int* key,
-                                                     const int* rank, const int* bscan, const int* ext_old, int* perm,
-                                                     int* ext_new) {
+                                                     const int* rank, const int* bscan, const int* remap,
+                                                     const int* ext_old, int* perm, int* ext_new) {
     const InstDev& I = inst[chunk_inst[blockIdx.x]];
     const long long p = (long long)blockIdx.x * kChunk + threadIdx.x;
     if (p - I.pbeg >= I.n) return;
-    const long long q = I.pbeg + (bscan[key[p]] - I.ext_off) + rank[p];
+    const long long q = I.pbeg + (remap[bscan[key[p]] + rank[p]] - I.ext_off);
     perm[q] = (int)p;
     ext_new[q] = ext_old[p];
 }
@@ -1586,7 +1621,7 @@ cudaError_t launch_state_to_ext(long long ncap, long long nslots, const int* ext
 
 cudaError_t launch_sort(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap, int n_keys,
                         const float* state, float* state_out, const int* ext_old, int* ext_new, int* key, int* rank,
-                        int* bcount, int* bscan, int* part, int* perm, cudaStream_t st) {
+                        int* bcount, int* bscan, int* part, int* remap, int* perm, cudaStream_t st) {
     if (n_chunks == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(bcount, 0, (size_t)n_keys * sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -1597,7 +1632,8 @@ cudaError_t launch_sort(const InstDev* inst, const int* chunk_inst, int n_chunks
     k_scan_add<<<(n_keys + 255) / 256, 256, 0, st>>>(bscan, part, n_keys);
     e = cudaMemcpyAsync(ext_new, ext_old, (size_t)ncap * sizeof(int), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
-    k_sort_perm<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, key, rank, bscan, ext_old, perm, ext_new);
+    k_sort_interleave<<<n_keys / 64, 64, 0, st>>>(bcount, bscan, remap);
+    k_sort_perm<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, key, rank, bscan, remap, ext_old, perm, ext_new);
     k_permute<<<n_chunks, kChunk, 0, st>>>(inst, chunk_inst, ncap, perm, state, state_out);
     return cudaGetLastError();
 }

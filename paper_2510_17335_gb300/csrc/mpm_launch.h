@@ -31,12 +31,14 @@ cudaError_t launch_adj_from_ext(long long ncap, long long nslots, const int* ext
                                 const float* gv, float* adj, cudaStream_t st);
 cudaError_t launch_state_to_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* s, float* x,
                                 float* v, float* C, float* F, cudaStream_t st);
-// reorder the particles of every instance by cell (n_keys = cells of all
-// instances): state -> state_out, ext_old -> ext_new, perm[new] = old; 6 kernels
+// reorder the particles of every instance by grid block, rank-major inside
+// a block (n_keys = cells of all instances, 64 per block): state ->
+// state_out, ext_old -> ext_new, perm[new] = old; remap holds one int per
+// particle (scratch); 7 kernels
 cudaError_t launch_sort(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap, int n_keys,
                         const float* state, float* state_out, const int* ext_old, int* ext_new, int* key, int* rank,
-                        int* bcount, int* bscan, int* part, int* perm, cudaStream_t st);
-constexpr int kSortLaunches = 6;
+                        int* bcount, int* bscan, int* part, int* remap, int* perm, cudaStream_t st);
+constexpr int kSortLaunches = 7;
 // dst[perm[q]] = src[q] for all 24 components
 cudaError_t launch_unpermute(const InstDev* inst, const int* chunk_inst, int n_chunks, long long ncap, const int* perm,
                              const float* src, float* dst, cudaStream_t st);
