@@ -69,11 +69,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="shared-memory tile scatter (1) or global atomics (0)")
     ap.add_argument("--sort", type=int, default=0, help="sort particles by cell every n substeps (0: never)")
+    ap.add_argument("--tune-substeps", type=int, default=20,
+                    help="trial substeps of mpm_autotune before timing (0: keep the default launch shape)")
     ap.add_argument("--batch", type=int, default=64, help="instances of the batched-vs-serial leg (0: skip)")
-    ap.add_argument("--sysid", type=int, default=0,
-                    help="candidates of the system-identification leg (0: skip; it takes minutes)")
+    ap.add_argument("--sysid", type=int, default=8,
+                    help="candidates of the system-identification leg (0: skip; 32 x 1500 substeps takes minutes)")
     ap.add_argument("--sysid-substeps", type=int, default=300)
     ap.add_argument("--sysid-iters", type=int, default=30)
+    ap.add_argument("--full-substeps", type=int, default=2000,
+                    help="substeps of the whole-rollout leg (0: skip); the 1M bed's rollout is 2,000")
+    ap.add_argument("--full-steps", type=int, default=2)
     ap.add_argument("--batch-substeps", type=int, default=500, help="substeps of each fwd+bwd loop of the batched leg (the uneven-batch workload runs 500)")
     return ap.parse_args()
 
@@ -299,6 +304,61 @@ def batched_vs_serial(n_inst: int, nsub: int, steps: int, sort_every: int):
 
 
 # --------------------------------------------------------------------------
+# the whole rollout of the 1M bed: 2,000 substeps fwd+bwd with recomputation
+# --------------------------------------------------------------------------
+def full_rollout(nsub: int, steps: int):
+    """fwd+bwd of the skill's whole rollout of the 1M bed from its initial
+    state: a recorded forward of nsub substeps (checkpoint interval K from the
+    free memory), the MSE loss and the backward, which reverses the last
+    segment from the record and recomputes every earlier one from its
+    checkpoint. Timed with CUDA events on the library's stream after two
+    warm-up steps (allocation, CUDA-graph capture)."""
+    import numpy as np
+    import torch
+
+    from paper_2510_17335_gb300 import mpm
+    from paper_2510_17335_gb300 import workloads as W
+
+    w = W.cfg_1m()
+    N = w.n
+    nodes = int(np.prod([-(-r // 4) * 4 for r in w.res]))
+    slot_state, slot_grid = 96 * N, 32 * nodes + nodes // 8 + 96 * N
+    K = auto_checkpoint(nsub, slot_state, slot_grid, torch.cuda.mem_get_info()[0])
+    n_seg = -(-nsub // K)
+    last = nsub - (n_seg - 1) * K
+    stream = torch.cuda.Stream()
+    sim = mpm.simulation_from_workloads([w], mpm.make_options(checkpoint_every=K))
+    sim.set_stream(stream.cuda_stream)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.stream(stream):
+        target = (torch.from_numpy(w.x0).to(dev) + torch.tensor([0.003, -0.002, 0.001], device=dev)).contiguous()
+        dldx = torch.empty((N, 3), device=dev)
+
+        def step():
+            sim.reset()
+            sim.forward(nsub, record=True)
+            sim.loss_mse(target, grad_out=dldx)
+            return sim.backward(dL_dx=dldx)
+
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            gm, _ = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    sim.close()
+    return {"workload": "bed1m_grid128, the skill's whole rollout from the initial bed",
+            "substeps": nsub, "checkpoint_every": K, "segments": n_seg, "recomputed_substeps": nsub - last,
+            "value": N * nsub / (ms / 1e3), "unit": "particle-substeps/s", "ms_per_step": ms, "steps": steps,
+            "finite_gradient": bool(np.isfinite(gm).all()),
+            "timing": "CUDA events on the library's stream, after 2 warm-up steps (allocation, graph capture)"}
+
+
+# --------------------------------------------------------------------------
 # system identification: wall clock to 5% parameter error, batched vs serial
 # --------------------------------------------------------------------------
 def sysid_leg(n_cand: int, nsub: int, iters: int):
@@ -310,18 +370,25 @@ def sysid_leg(n_cand: int, nsub: int, iters: int):
     w = W.cfg_sysid(n_substeps=nsub)
     rng = np.random.default_rng(W.SEED_BASE + 6)
     truth = (w.E, w.nu, w.rho, w.phi_deg)
-    free = (True, False, False, True)               # E and phi; nu, rho known
-    starts = [(rng.uniform(*sysid.RANGES[0]), w.nu, w.rho, rng.uniform(*sysid.RANGES[3])) for _ in range(n_cand)]
+    free = (True, True, False, True)                # E, nu and phi; rho known (only E/rho moves the bed)
+    starts = [(rng.uniform(*sysid.RANGES[0]), rng.uniform(0.2, 0.4), w.rho, rng.uniform(*sysid.RANGES[3]))
+              for _ in range(n_cand)]
     grid = mpm.make_obs_grid((0.5, 0.5), 0.5, 40)
+    names, _ = sysid.identifiable(np.asarray(truth)[None, :], free)
     out = {"candidates": n_cand, "particles_per_candidate": w.n, "grid": "64^3", "substeps": nsub,
-           "free": ["E", "phi"], "truth": list(truth), "line_search": "hmd (5 multiples, Sec. III-F)",
-           "optimiser": "RMSprop beta 0.9, step sizes E 1e4, phi 1; adjoint clipping 1e4"}
+           "iterations": iters, "free": ["E", "nu", "phi"], "identified": names, "truth": list(truth),
+           "line_search": "hmd (5 multiples, Sec. III-F)",
+           "optimiser": "RMSprop beta 0.9, step sizes E 1e4, nu 0.01, phi 1; adjoint clipping 1e4",
+           "criterion": "every candidate within 5% on the identified quantities (K = E / (3 (1 - 2 nu)), phi)"}
     for mode in ("batched", "serial"):
         r = sysid.identify(w, truth, starts, nsub, iters, grid, free=free, batched=(mode == "batched"))
+        fin = r.params[-1]
         out[mode] = {"iterations_to_5pct": r.converged_at, "seconds_to_5pct": r.seconds_to_converge,
                      "seconds_per_iteration": r.seconds[-1] / len(r.seconds),
                      "final_max_rel_error": float(np.max(r.errors[-1])),
-                     "final_params": np.round(r.params[-1], 4).tolist()}
+                     "final_rel_error_E_nu": [float(np.max(np.abs(fin[:, 0] / w.E - 1))),
+                                              float(np.max(np.abs(fin[:, 1] / w.nu - 1)))],
+                     "final_params": np.round(fin, 4).tolist()}
     b, s_ = out["batched"]["seconds_per_iteration"], out["serial"]["seconds_per_iteration"]
     out["speedup_per_iteration"] = s_ / b
     return out
@@ -373,6 +440,9 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         # rollout start state: the skill at substep `start` (shovel inserting)
         sim.forward(args.start)
+        # register caps of the particle kernels and the sort interval, timed
+        # from that state (which the tuner restores)
+        tuned = sim.autotune(args.tune_substeps) if args.tune_substeps > 0 else None
         st0 = {k: torch.empty((N, 3) if k in "xv" else (N, 3, 3), device=dev) for k in "xvCF"}
         sim.get_state(device_out=st0)
         target = (torch.from_numpy(w.x0).to(dev) + torch.tensor([0.003, -0.002, 0.001], device=dev)).contiguous()
@@ -516,6 +586,9 @@ def run_ours(args):
                  "fwd_bytes_per_particle_substep": FWD_BYTES,
                  "fwd_frac": round(FWD_BYTES * N * S * args.steps / (fms / 1e3) / 1e9 / peak, 4),
                  "peak_kind": f"{peak_kind} hbm_gbs"}
+    # the other legs need the main leg's memory
+    sim.close()
+    full = full_rollout(args.full_substeps, args.full_steps) if args.full_substeps > 0 else None
     batch = None
     if args.batch > 0:
         batch = batched_vs_serial(args.batch, args.batch_substeps, 3, args.sort)
@@ -536,12 +609,14 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD,
                    "substeps_per_step": S, "checkpoint_every": K, "start_substep": args.start,
-                   "tile_scatter": args.tile, "sort_every": args.sort,
+                   "tile_scatter": args.tile, "sort_every": tuned["sort_every"] if tuned else args.sort,
+                   "autotune": ({"trial_substeps": args.tune_substeps, **tuned} if tuned else None),
                    "record_bytes": record_bytes,
                    "l2": f"inputs larger than L2 (96 MB state, {record_bytes / 1e9:.1f} GB of recorded states and grids per step)",
                    "parallelism": f"replicas x{ws}"},
         "fwd_value": fwd_value, "fwd_ms_per_step": fms / args.steps,
         "roofline": roof, "roofline_step": roof_step, "alu": alu, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "full_rollout": full,
         "batched_vs_serial": batch,
         **({"sysid": sid} if sid is not None else {}),
         "kernels": kernels, "clocks": clk,

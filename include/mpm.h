@@ -271,13 +271,29 @@ int mpm_get_action_grad(mpm_handle* h, int inst, double* dL_dactions, double* dL
  * sum_p rho V_p up to rounding. */
 int mpm_grid_mass(mpm_handle* h, double* mass);
 
-/* Autotuner: from the current state, time a recorded forward of
- * trial_substeps plus its backward (CUDA events) for each candidate of
- * {global-atomic or shared-tile scatter} x {no sort, sort by cell}; keep the
- * fastest as the handle's tile_scatter and sort_every (sorting then happens
- * once per checkpoint segment) and write them to chosen[2] (may be NULL).
- * The state, the substep counter and the options not tuned are restored;
- * any record is dropped. */
+/* Launch shape of the particle kernels: the register cap each is compiled
+ * for, as the minimum number of resident CTAs per SM, shape[0] k_p2g (3 or
+ * 4), shape[1] k_g2p (3 or 4), shape[2] the fused adjoint k_p2g_g2p_bwd (2,
+ * 3 or 4); defaults 4, 4, 3 (the fastest of measured sweeps on the
+ * 1M-particle bed). Other values: MPM_ERR_INVALID_ARG. A change drops the
+ * handle's CUDA graphs. */
+int mpm_set_launch_shape(mpm_handle* h, const int shape[3]);
+int mpm_get_launch_shape(mpm_handle* h, int shape[3]);
+
+/* Autotuner: from the current state, times a recorded forward of
+ * trial_substeps plus its backward for each candidate and keeps the fastest:
+ * first the register caps of mpm_set_launch_shape (every kernel's
+ * candidates in the same trials, each kernel timed per launch with CUDA
+ * events, each keeping its fastest cap), then, with those caps, no sort
+ * against a sort by cell once per checkpoint segment (sort_every). Writes
+ * chosen[0] = tile_scatter (not tuned), chosen[1] = sort_every (may be
+ * NULL); mpm_get_launch_shape gives the caps. The choice is cached for the
+ * process per device and workload (instance count, particle counts, grids):
+ * a later call for the same workload with trial_substeps no larger than the
+ * cached trial applies it without timing. The state, its particle order,
+ * the substep counter and the options not tuned are restored on every
+ * return, errors included; any record is dropped and the kernel-timing
+ * counters are reset. */
 int mpm_autotune(mpm_handle* h, int trial_substeps, int* chosen);
 
 /* Set the substep counter (the index into the shovel pose tables) of the

@@ -10,6 +10,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -195,6 +197,7 @@ struct mpm_handle {
     std::vector<char> seg_sorted;
     int64_t since_sort = 1LL << 40;
     Profiler prof;
+    LaunchShape shape;                // register caps of the particle kernels
     // CUDA graphs of repeated identical forward / backward calls
     std::vector<struct GraphEntry*> graphs;
     int64_t graph_tick = 0;
@@ -509,12 +512,12 @@ int run_kernel(mpm_handle* h, KernelId id, const AdjArgs& A) {
     if (h->prof.on) {
         Profiler::Pending p{(int)id, h->prof.get(), h->prof.get()};
         CK(cudaEventRecord(p.a, h->stream));
-        CK(launch_kernel(id, A, h->stream));
+        CK(launch_kernel(id, A, h->shape, h->stream));
         CK(cudaEventRecord(p.b, h->stream));
         h->prof.pending.push_back(p);
         if (h->prof.pending.size() > 65536) h->prof.flush();
     } else {
-        CK(launch_kernel(id, A, h->stream));
+        CK(launch_kernel(id, A, h->shape, h->stream));
     }
     h->launches++;
     return MPM_OK;
@@ -524,12 +527,12 @@ int run_fused(mpm_handle* h, KernelId id, const AdjArgs& A, const AdjArgs& G) {
     if (h->prof.on) {
         Profiler::Pending p{(int)id, h->prof.get(), h->prof.get()};
         CK(cudaEventRecord(p.a, h->stream));
-        CK(launch_fused(id, A, G, h->stream));
+        CK(launch_fused(id, A, G, h->shape, h->stream));
         CK(cudaEventRecord(p.b, h->stream));
         h->prof.pending.push_back(p);
         if (h->prof.pending.size() > 65536) h->prof.flush();
     } else {
-        CK(launch_fused(id, A, G, h->stream));
+        CK(launch_fused(id, A, G, h->shape, h->stream));
     }
     h->launches++;
     return MPM_OK;
@@ -1469,75 +1472,207 @@ int mpm_get_action_grad(mpm_handle* h, int inst, double* dL_dactions, double* dL
     return MPM_OK;
 }
 
+int mpm_set_launch_shape(mpm_handle* h, const int shape[3]) {
+    if (!h || !shape) return MPM_ERR_INVALID_ARG;
+    if (shape[0] < 3 || shape[0] > 4 || shape[1] < 3 || shape[1] > 4 || shape[2] < 2 || shape[2] > 4)
+        return MPM_ERR_INVALID_ARG;
+    if (h->shape.p2g != shape[0] || h->shape.g2p != shape[1] || h->shape.fused != shape[2]) {
+        h->shape.p2g = shape[0];
+        h->shape.g2p = shape[1];
+        h->shape.fused = shape[2];
+        drop_graphs(h);   // the captured launches name the old instantiations
+    }
+    return MPM_OK;
+}
+
+int mpm_get_launch_shape(mpm_handle* h, int shape[3]) {
+    if (!h || !shape) return MPM_ERR_INVALID_ARG;
+    shape[0] = h->shape.p2g;
+    shape[1] = h->shape.g2p;
+    shape[2] = h->shape.fused;
+    return MPM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Choices of the autotuner per workload (device, instances, their particle
+// counts and grids), kept for the life of the process.
+struct TuneChoice {
+    int trial = 0;
+    int shape[3] = {4, 4, 3};
+    int sort_every = 0;   // 0: no sort, else sort once per checkpoint segment
+};
+std::mutex g_tune_mu;
+std::map<std::vector<int64_t>, TuneChoice> g_tune_cache;
+
+std::vector<int64_t> tune_key(const mpm_handle* h) {
+    std::vector<int64_t> k = {h->device, (int64_t)h->inst.size()};
+    for (const Instance& I : h->inst) {
+        k.push_back(I.n);
+        for (int a = 0; a < 3; a++) k.push_back(I.cfg.res[a]);
+    }
+    return k;
+}
+
+// Everything mpm_autotune changes while it times candidates, put back on
+// every way out: the state and its particle order, the substep counter, the
+// options, the launch shape, the profiler switch; the CUDA events and the
+// saved copies are released. Any record is dropped.
+struct TuneGuard {
+    mpm_handle* h;
+    DevBuf<float> save;
+    DevBuf<int> save_ext;
+    int64_t substep0 = 0;
+    mpm_options opt0;
+    LaunchShape shape0;
+    int tile0 = 0;
+    bool prof0 = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    bool saved = false;
+    explicit TuneGuard(mpm_handle* hh) : h(hh) {
+        substep0 = h->substep;
+        opt0 = h->opt;
+        shape0 = h->shape;
+        tile0 = h->tile_scatter;
+        prof0 = h->prof.on;
+    }
+    int save_state() {
+        const size_t state_floats = (size_t)h->ncap * kStateComps;
+        RK(save.ensure(state_floats, h->device_bytes));
+        RK(save_ext.ensure((size_t)h->ncap, h->device_bytes));
+        CK(cudaMemcpyAsync(save.p, h->d_state.p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(save_ext.p, h->d_ext_of_slot.p, (size_t)h->ncap * sizeof(int), cudaMemcpyDeviceToDevice,
+                           h->stream));
+        saved = true;
+        return MPM_OK;
+    }
+    // the saved state again, as the start of a trial
+    int restore_state() {
+        const size_t state_floats = (size_t)h->ncap * kStateComps;
+        CK(cudaMemcpyAsync(h->d_state.p, save.p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->d_ext_of_slot.p, save_ext.p, (size_t)h->ncap * sizeof(int), cudaMemcpyDeviceToDevice,
+                           h->stream));
+        h->substep = substep0;
+        h->recording = false;
+        h->seg_valid = -1;
+        h->since_sort = 1LL << 40;
+        return MPM_OK;
+    }
+    ~TuneGuard() {
+        if (saved) restore_state();
+        cudaStreamSynchronize(h->stream);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        h->device_bytes -= (int64_t)(save.n * sizeof(float) + save_ext.n * sizeof(int));
+        save.release();
+        save_ext.release();
+        h->prof.reset();
+        h->prof.on = prof0;
+        h->have_grad = false;
+        cudaGetLastError();
+    }
+    // put the options and the shape back (on failure: everything as found)
+    void revert() {
+        h->opt = opt0;
+        h->tile_scatter = tile0;
+        if (h->shape.p2g != shape0.p2g || h->shape.g2p != shape0.g2p || h->shape.fused != shape0.fused) {
+            h->shape = shape0;
+            drop_graphs(h);
+        }
+    }
+};
+
+// one trial from the saved state: a recorded forward and its backward;
+// the elapsed device time in ms
+int tune_trial(mpm_handle* h, TuneGuard& g, int trial_substeps, float* ms) {
+    RK(g.restore_state());
+    CK(cudaEventRecord(g.e0, h->stream));
+    RK(mpm_forward(h, trial_substeps, 1));
+    RK(mpm_backward(h, nullptr, nullptr, 1, nullptr, nullptr));
+    CK(cudaEventRecord(g.e1, h->stream));
+    CK(cudaEventSynchronize(g.e1));
+    CK(cudaEventElapsedTime(ms, g.e0, g.e1));
+    return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int mpm_autotune(mpm_handle* h, int trial_substeps, int* chosen) {
     if (!h || trial_substeps < 1 || trial_substeps > 100000) return MPM_ERR_INVALID_ARG;
     RK(set_device(h));
-    // the state and substep this call starts from are restored afterwards
-    const size_t state_floats = (size_t)h->ncap * kStateComps;
-    DevBuf<float> save;
-    DevBuf<int> save_ext;
-    RK(save.ensure(state_floats, h->device_bytes));
-    RK(save_ext.ensure((size_t)h->ncap, h->device_bytes));
-    CK(cudaMemcpyAsync(save.p, h->d_state.p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
-    CK(cudaMemcpyAsync(save_ext.p, h->d_ext_of_slot.p, (size_t)h->ncap * sizeof(int), cudaMemcpyDeviceToDevice,
-                       h->stream));
-    const int64_t substep0 = h->substep;
-    const mpm_options opt0 = h->opt;
-    struct Cand {
-        int tile, sort;
-    };
-    const Cand cands[4] = {{0, 0}, {1, 0}, {0, trial_substeps}, {1, trial_substeps}};
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_i = 0, rc = MPM_OK;
-    for (int c = 0; c < 4 && rc == MPM_OK; c++) {
-        for (int rep = 0; rep < 2 && rc == MPM_OK; rep++) {   // the first run allocates
-            CK(cudaMemcpyAsync(h->d_state.p, save.p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice,
-                               h->stream));
-            CK(cudaMemcpyAsync(h->d_ext_of_slot.p, save_ext.p, (size_t)h->ncap * sizeof(int),
-                               cudaMemcpyDeviceToDevice, h->stream));
-            h->substep = substep0;
-            h->recording = false;
-            h->seg_valid = -1;
-            h->tile_scatter = cands[c].tile;
-            h->opt.sort_every = cands[c].sort;
-            h->since_sort = 1LL << 40;
-            CK(cudaEventRecord(e0, h->stream));
-            rc = mpm_forward(h, trial_substeps, 1);
-            if (rc == MPM_OK) rc = mpm_backward(h, nullptr, nullptr, 1, nullptr, nullptr);
-            CK(cudaEventRecord(e1, h->stream));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep == 1 && ms < best) {
-                best = ms;
-                best_i = c;
-            }
+    const std::vector<int64_t> key = tune_key(h);
+    TuneChoice best;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && it->second.trial >= trial_substeps) {
+            best = it->second;
+            cached = true;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    CK(cudaMemcpyAsync(h->d_state.p, save.p, state_floats * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->d_ext_of_slot.p, save_ext.p, (size_t)h->ncap * sizeof(int), cudaMemcpyDeviceToDevice,
-                       h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    h->device_bytes -= (int64_t)(save.n * sizeof(float) + save_ext.n * sizeof(int));
-    save.release();
-    save_ext.release();
-    h->substep = substep0;
-    h->recording = false;
-    h->seg_valid = -1;
-    h->have_grad = false;
-    h->opt = opt0;
-    if (rc != MPM_OK) {
-        h->tile_scatter = opt0.tile_scatter ? 1 : 0;
-        return rc;
+    if (!cached) {
+        TuneGuard g(h);
+        RK(g.save_state());
+        CK(cudaEventCreate(&g.e0));
+        CK(cudaEventCreate(&g.e1));
+        int rc = MPM_OK;
+        // 1. register caps: every kernel's candidates in the same trials
+        // (timed per launch by the profiler), each kernel keeps its fastest
+        const int shapes[3][3] = {{3, 3, 2}, {4, 4, 3}, {4, 4, 4}};
+        double kbest[3] = {1e300, 1e300, 1e300};
+        const KernelId kid[3] = {KernelId::P2G, KernelId::G2P, KernelId::P2GG2PBwd};
+        h->opt.sort_every = 0;
+        for (int c = 0; c < 3 && rc == MPM_OK; c++) {
+            rc = mpm_set_launch_shape(h, shapes[c]);
+            for (int rep = 0; rep < 2 && rc == MPM_OK; rep++) {   // the first run allocates
+                h->prof.reset();
+                h->prof.on = true;
+                float ms = 0.f;
+                rc = tune_trial(h, g, trial_substeps, &ms);
+                h->prof.flush();
+                h->prof.on = false;
+                if (rc != MPM_OK || rep == 0) continue;
+                for (int k = 0; k < 3; k++) {
+                    const int id = (int)kid[k];
+                    if (h->prof.count[id] == 0) continue;
+                    const double avg = h->prof.total_ms[id] / (double)h->prof.count[id];
+                    // candidates that repeat an earlier cap are not new
+                    bool seen = false;
+                    for (int e = 0; e < c; e++) seen = seen || shapes[e][k] == shapes[c][k];
+                    if (!seen && avg < kbest[k]) {
+                        kbest[k] = avg;
+                        best.shape[k] = shapes[c][k];
+                    }
+                }
+            }
+        }
+        // 2. sorting by cell (once per checkpoint segment) or not, with those caps
+        float tbest = 1e30f;
+        for (int srt = 0; srt < 2 && rc == MPM_OK; srt++) {
+            rc = mpm_set_launch_shape(h, best.shape);
+            h->opt.sort_every = srt ? std::max(h->opt.checkpoint_every, 1) : 0;
+            for (int rep = 0; rep < 2 && rc == MPM_OK; rep++) {
+                float ms = 0.f;
+                rc = tune_trial(h, g, trial_substeps, &ms);
+                if (rc == MPM_OK && rep == 1 && ms < tbest) {
+                    tbest = ms;
+                    best.sort_every = h->opt.sort_every;
+                }
+            }
+        }
+        g.revert();
+        if (rc != MPM_OK) return rc;
+        best.trial = trial_substeps;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
     }
-    h->tile_scatter = cands[best_i].tile;
-    h->opt.tile_scatter = cands[best_i].tile;
-    h->opt.sort_every = cands[best_i].sort ? std::max(h->opt.checkpoint_every, 1) : 0;
+    RK(mpm_set_launch_shape(h, best.shape));
+    h->opt.sort_every = best.sort_every;
     h->since_sort = 1LL << 40;
     if (chosen) {
         chosen[0] = h->opt.tile_scatter;

@@ -28,26 +28,18 @@
 #include "mpm_device.cuh"
 #include "mpm_launch.h"
 
-// minimum resident CTAs per SM of the particle kernels (register caps; the
-// defaults are the fastest of a measured sweep on the 1M-particle bed)
-#ifndef MPM_MINB_P2G
-#define MPM_MINB_P2G 4
-#endif
 // 1: the substep kernels use programmatic dependent launch (launch_pdl)
 #ifndef MPM_PDL
 #define MPM_PDL 1
 #endif
-#ifndef MPM_MINB_G2P
-#define MPM_MINB_G2P 4
-#endif
+// minimum resident CTAs per SM (register caps) of the adjoint kernels that
+// run once per checkpoint segment; those of k_p2g, k_g2p and the fused
+// adjoint are template parameters chosen per handle (LaunchShape)
 #ifndef MPM_MINB_G2P_BWD
 #define MPM_MINB_G2P_BWD 3
 #endif
 #ifndef MPM_MINB_P2G_BWD
 #define MPM_MINB_P2G_BWD 3
-#endif
-#ifndef MPM_MINB_FUSED_BWD
-#define MPM_MINB_FUSED_BWD 3
 #endif
 
 namespace mpm {
@@ -235,7 +227,8 @@ __device__ __forceinline__ void p2g_store_affine(const InstDev& I, const StepArg
 // P2G with the constitutive step, FP32. A particle whose deformation is
 // ill-conditioned for FP32 (see needs_fp64) is listed for k_p2g_fp64, which
 // does its constitutive step and transfer.
-__global__ void __launch_bounds__(kChunk, MPM_MINB_P2G) k_p2g(StepArgs a) {
+template <int MINB>
+__global__ void __launch_bounds__(kChunk, MINB) k_p2g(StepArgs a) {
     wait_previous_grid();
     __shared__ TileSmem T;
     __shared__ InstDev sI;
@@ -503,7 +496,8 @@ __device__ __forceinline__ void g2p_particle(const InstDev& I, const StepArgs& a
         }
 }
 
-__global__ void __launch_bounds__(kChunk, MPM_MINB_G2P) k_g2p(StepArgs a) {
+template <int MINB>
+__global__ void __launch_bounds__(kChunk, MINB) k_g2p(StepArgs a) {
     wait_previous_grid();
     __shared__ InstDev sI;
     const int inst = a.chunk_inst[blockIdx.x];
@@ -1164,7 +1158,8 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_P2G_BWD) k_p2g_bwd_reg(AdjArg
 // the P2G adjoint of substep k (A) and the G2P adjoint of substep k-1 (G) in
 // one pass over the particles: the x, v, C adjoints of state k stay in
 // registers. G.gacc is the other grid-adjoint buffer (zero on entry).
-__global__ void __launch_bounds__(kChunk, MPM_MINB_FUSED_BWD) k_p2g_g2p_bwd(AdjArgs A, AdjArgs G) {
+template <int MINB>
+__global__ void __launch_bounds__(kChunk, MINB) k_p2g_g2p_bwd(AdjArgs A, AdjArgs G) {
     wait_previous_grid();
     p2g_bwd_cta<false, true>(A, &G);
 }
@@ -1546,16 +1541,24 @@ static cudaError_t launch_pdl(void (*k)(P...), unsigned grid, unsigned block, cu
 // full wave of 256-thread CTAs (8 per SM), grid-stride beyond
 static inline int list_ctas(int n_blocks) { return std::min(grid_ctas(n_blocks), kListCtas); }
 
-cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
+// the instantiation of a particle kernel for a register cap (minimum
+// resident CTAs per SM); caps outside the instantiated set take the nearest
+static unsigned p2g_minb(int m) { return m <= 3 ? 3 : 4; }
+
+cudaError_t launch_kernel(KernelId id, const AdjArgs& A, const LaunchShape& ls, cudaStream_t s) {
     const StepArgs& a = A.f;
     const bool particle_kernel = id == KernelId::P2G || id == KernelId::G2P || id == KernelId::G2PBwd ||
                                  id == KernelId::P2GBwd || id == KernelId::P2GFp64 ||
                                  id == KernelId::P2GBwdFp64;
     if ((particle_kernel && a.n_chunks <= 0) || (!particle_kernel && a.n_blocks <= 0)) return cudaSuccess;
     switch (id) {
-        case KernelId::P2G: return launch_pdl(k_p2g, a.n_chunks, kChunk, s, a);
+        case KernelId::P2G:
+            return p2g_minb(ls.p2g) == 3 ? launch_pdl(k_p2g<3>, a.n_chunks, kChunk, s, a)
+                                         : launch_pdl(k_p2g<4>, a.n_chunks, kChunk, s, a);
         case KernelId::Grid: return launch_pdl(k_grid, list_ctas(a.n_blocks), 256, s, a);
-        case KernelId::G2P: return launch_pdl(k_g2p, a.n_chunks, kChunk, s, a);
+        case KernelId::G2P:
+            return p2g_minb(ls.g2p) == 3 ? launch_pdl(k_g2p<3>, a.n_chunks, kChunk, s, a)
+                                         : launch_pdl(k_g2p<4>, a.n_chunks, kChunk, s, a);
         case KernelId::G2PBwd: return launch_pdl(k_g2p_bwd, a.n_chunks, kChunk, s, A);
         case KernelId::GridBwd: return launch_pdl(k_grid_bwd, list_ctas(a.n_blocks), 256, s, A);
         case KernelId::P2GBwd:
@@ -1579,12 +1582,15 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fused(KernelId id, const AdjArgs& A, const AdjArgs& G, cudaStream_t s) {
+cudaError_t launch_fused(KernelId id, const AdjArgs& A, const AdjArgs& G, const LaunchShape& ls, cudaStream_t s) {
     const StepArgs& a = A.f;
     if (a.n_chunks <= 0) return cudaSuccess;
     if (!a.spec || A.gscale || a.tile) return cudaErrorInvalidValue;
     switch (id) {
-        case KernelId::P2GG2PBwd: return launch_pdl(k_p2g_g2p_bwd, a.n_chunks, kChunk, s, A, G);
+        case KernelId::P2GG2PBwd:
+            if (ls.fused <= 2) return launch_pdl(k_p2g_g2p_bwd<2>, a.n_chunks, kChunk, s, A, G);
+            if (ls.fused == 3) return launch_pdl(k_p2g_g2p_bwd<3>, a.n_chunks, kChunk, s, A, G);
+            return launch_pdl(k_p2g_g2p_bwd<4>, a.n_chunks, kChunk, s, A, G);
         case KernelId::P2GG2PBwdFp64: return launch_pdl(k_p2g_g2p_bwd_fp64, kFp64Ctas, kFp64Threads, s, A, G);
         default: return cudaErrorInvalidValue;
     }

@@ -14,12 +14,20 @@ constexpr int kFp64Ctas = 152;   // CTAs of the FP64 fix-up kernels (grid-stride
 constexpr int kFp64Threads = 128;
 constexpr int kListCtas = 152 * 8;   // CTAs of the grid kernels that walk the touched-block list
 
+// Register caps of the particle kernels, as the minimum number of resident
+// CTAs per SM each is compiled for: k_p2g and k_g2p 3 or 4, the fused
+// adjoint 2, 3 or 4. The defaults are the fastest of measured sweeps on the
+// 1M-particle bed; mpm_autotune times the alternatives for a handle.
+struct LaunchShape {
+    int p2g = 4, g2p = 4, fused = 3;
+};
+
 // one substep kernel; forward kernels read only A.f
-cudaError_t launch_kernel(KernelId id, const AdjArgs& A, cudaStream_t s);
+cudaError_t launch_kernel(KernelId id, const AdjArgs& A, const LaunchShape& ls, cudaStream_t s);
 // the fused adjoint (P2GG2PBwd, P2GG2PBwdFp64): the P2G adjoint of substep k
 // (A) with the G2P adjoint of substep k-1 (G, whose gacc is the other grid
 // adjoint buffer); not with the regularisers or the scatter tile
-cudaError_t launch_fused(KernelId id, const AdjArgs& A, const AdjArgs& G, cudaStream_t s);
+cudaError_t launch_fused(KernelId id, const AdjArgs& A, const AdjArgs& G, const LaunchShape& ls, cudaStream_t s);
 cudaError_t launch_state_from_ext(long long ncap, long long nslots, const int* ext_of_slot, const float* x,
                                   const float* v, const float* C, const float* F, float* s, cudaStream_t st);
 // statistics of the x, v, F adjoints of a state for the regularisers of

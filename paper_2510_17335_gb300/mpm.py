@@ -104,6 +104,8 @@ EXPORTS = {
     "mpm_grid_mass": (_ip, [_vp, _dp]),
     "mpm_set_substep": (_ip, [_vp, ctypes.c_int64]),
     "mpm_autotune": (_ip, [_vp, _ip, ctypes.POINTER(ctypes.c_int)]),
+    "mpm_set_launch_shape": (_ip, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "mpm_get_launch_shape": (_ip, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "mpm_profile": (_ip, [_vp, _ip]),
     "mpm_profile_read": (_ip, [_vp, _ip, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "mpm_kernel_name": (ctypes.c_char_p, [_ip]),
@@ -359,9 +361,20 @@ class Simulation:
         check(lib().mpm_synchronize(self.h), "mpm_synchronize")
 
     def autotune(self, trial_substeps: int = 20) -> dict:
+        """mpm_autotune: the chosen sort interval and register caps."""
         c = (ctypes.c_int * 2)()
         check(lib().mpm_autotune(self.h, int(trial_substeps), c), "mpm_autotune")
-        return {"tile_scatter": c[0], "sort_every": c[1]}
+        return {"tile_scatter": c[0], "sort_every": c[1], "launch_shape": self.launch_shape()}
+
+    def launch_shape(self) -> dict:
+        """Register caps (minimum resident CTAs per SM) of k_p2g, k_g2p and the fused adjoint."""
+        c = (ctypes.c_int * 3)()
+        check(lib().mpm_get_launch_shape(self.h, c), "mpm_get_launch_shape")
+        return {"p2g": c[0], "g2p": c[1], "fused": c[2]}
+
+    def set_launch_shape(self, p2g: int, g2p: int, fused: int):
+        c = (ctypes.c_int * 3)(int(p2g), int(g2p), int(fused))
+        check(lib().mpm_set_launch_shape(self.h, c), "mpm_set_launch_shape")
 
     def set_substep(self, s: int):
         check(lib().mpm_set_substep(self.h, int(s)), "mpm_set_substep")

@@ -10,9 +10,19 @@ forward and the one with the least height-map distance to the target map
 wins. The host only orchestrates; every rollout, loss, adjoint and height
 map runs in the library's kernels.
 
-Under a kinematic shovel the motion depends on E and rho only through E/rho
-(the momentum balance divided by the density), so positions identify the
-ratio, not both: rho is held at a known value unless it is freed.
+Which parameters the positions identify. Under a kinematic shovel the
+motion depends on E and rho only through E/rho (the momentum balance divided
+by the density), so positions identify the ratio, not both: rho is held at a
+known value unless it is freed. With E and nu both free the loop settles on
+the bulk modulus K = E / (3 (1 - 2 nu)), not on E and nu apart: the sand
+yields in shear (the Drucker-Prager cone bounds the deviatoric stress), so the
+elastic shear modulus barely moves the particles while the bulk response
+(settling, compaction ahead of the shovel) does. Measured on the batched
+identification workload: eight candidates from random starts in the ranges
+end within 2.4% of the true K with E anywhere in 108k-158k. The error the
+loop reports and converges on is therefore that of the identifiable
+quantities (``identifiable``): K (or E, or nu, whichever of them is free),
+divided by rho when rho is free too, and phi.
 """
 from __future__ import annotations
 
@@ -36,9 +46,10 @@ BETA = 0.9                            # RMSprop decay
 class SysIdResult:
     params: np.ndarray                  # [iterations + 1, n_cand, 4]
     losses: List[np.ndarray] = field(default_factory=list)   # MSE per iteration, [n_cand]
-    errors: List[np.ndarray] = field(default_factory=list)   # max relative error of the free parameters
+    errors: List[np.ndarray] = field(default_factory=list)   # max relative error of the identifiable quantities
     seconds: List[float] = field(default_factory=list)       # wall clock at the end of each iteration
     converged_at: Optional[int] = None  # first iteration after which every candidate is within tol
+                                        # on the identifiable quantities (see identifiable)
     seconds_to_converge: Optional[float] = None
 
 
@@ -58,9 +69,46 @@ def _auto_checkpoint(n_substeps: int, n_particles: int, n_nodes: int) -> int:
     return int(max(1, min(n_substeps, k)))
 
 
+def identifiable(theta: np.ndarray, free) -> tuple[list, np.ndarray]:
+    """The quantities the final positions identify, for candidates theta
+    [n, 4] (E, nu, rho, phi) with the given parameters free: names and
+    values [n, m]. The stiffness enters as E (nu fixed), nu (E fixed) or the
+    bulk modulus K = E / (3 (1 - 2 nu)) (both free), over rho when rho is
+    free (only the ratio moves the particles); rho alone, and phi, stand for
+    themselves."""
+    theta = np.atleast_2d(np.asarray(theta, np.float64))
+    free = np.asarray(free, bool)
+    E, nu, rho, phi = theta.T
+    names, cols = [], []
+    if free[0] or free[1]:
+        if free[0] and free[1]:
+            names.append("K")
+            cols.append(E / (3.0 * (1.0 - 2.0 * nu)))
+        elif free[0]:
+            names.append("E")
+            cols.append(E)
+        else:
+            names.append("nu")
+            cols.append(nu)
+        if free[2]:
+            names[-1] += "/rho"
+            cols[-1] = cols[-1] / rho
+    elif free[2]:
+        names.append("rho")
+        cols.append(rho)
+    if free[3]:
+        names.append("phi")
+        cols.append(phi)
+    return names, (np.stack(cols, axis=1) if cols else np.zeros((theta.shape[0], 0)))
+
+
 def _rel_error(theta: np.ndarray, truth: np.ndarray, free: np.ndarray) -> np.ndarray:
-    e = np.abs(theta - truth) / np.abs(truth)
-    return np.where(free[None, :], e, 0.0).max(axis=1)
+    """The largest relative error per candidate over the identifiable quantities."""
+    _, v = identifiable(theta, free)
+    _, t = identifiable(truth[None, :], free)
+    if v.shape[1] == 0:
+        return np.zeros(v.shape[0])
+    return (np.abs(v - t) / np.abs(t)).max(axis=1)
 
 
 class _Group:

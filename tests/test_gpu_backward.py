@@ -258,6 +258,48 @@ def test_fused_adjoint_equals_unfused(K):
     assert rel_err(ga1[0][0], ga0[0][0]).max() < 1e-3
 
 
+def test_non_finite_adjoint_seed_is_reported_and_the_handle_recovers():
+    """A NaN in the dL/dx seed spreads through the adjoint (the gradient
+    problem that Sec. III-E's clipping addresses): mpm_backward returns
+    MPM_ERR_NON_FINITE, and the same handle then gives, for a finite seed,
+    the gradients of a fresh handle: the material gradient within the 2e-2
+    bar, the state adjoints within three times the spread of two fresh runs
+    (float atomics reorder the sums from run to run)."""
+    w = W.cfg_small()
+    opts = mpm.make_options(checkpoint_every=16)
+    nsub = 40
+    g = np.full((w.n, 3), 1.0 / w.n, np.float32)
+    bad = g.copy()
+    bad[17, 1] = np.nan
+
+    def run(sim):
+        sim.reset()
+        sim.forward(nsub, record=True)
+        gm, _ = sim.backward(dL_dx=g)
+        return gm, sim.state_grad()
+
+    with mpm.simulation_from_workloads([w], opts) as sim:
+        sim.forward(nsub, record=True)
+        with pytest.raises(mpm.MpmError) as e:
+            sim.backward(dL_dx=bad)
+        assert e.value.code == -5
+        gm, sg = run(sim)
+    with mpm.simulation_from_workloads([w], opts) as fresh:
+        gm_ref, sg_ref = run(fresh)
+    with mpm.simulation_from_workloads([w], opts) as fresh2:
+        _, sg_ref2 = run(fresh2)
+    assert np.isfinite(gm).all()
+    print("recovered", gm[0], "fresh", gm_ref[0])
+    assert (rel_err(gm[0], gm_ref[0]) < 2e-2).all()
+    for k in ("x", "v", "C", "F"):
+        assert np.isfinite(sg[k]).all(), k
+        spread = np.linalg.norm(sg_ref2[k] - sg_ref[k])
+        dev = np.linalg.norm(sg[k] - sg_ref[k])
+        scale = np.linalg.norm(sg_ref[k])
+        print(k, "recovered - fresh", dev / scale, "fresh - fresh", spread / scale)
+        assert dev <= 3 * spread + 1e-3 * scale, k
+
+
 def test_backward_without_record_fails_cleanly():
     w = _contact_workload()
     with mpm.simulation_from_workloads([w]) as sim:

@@ -354,7 +354,40 @@ def test_autotune_restores_state_and_keeps_parity():
         for k in before:
             assert np.array_equal(before[k], after[k]), k
         assert choice["tile_scatter"] in (0, 1) and choice["sort_every"] >= 0
+        sh = choice["launch_shape"]
+        assert sh["p2g"] in (3, 4) and sh["g2p"] in (3, 4) and sh["fused"] in (2, 3, 4)
+        # the choice is cached for the workload: a second call gives it again
+        assert sim.autotune(6) == choice
         sim.forward(7)
         g = sim.get_state()
     ref = oracle_rollout(w, 10)
     _compare(g, ref, 10, f"bed8k after autotune {choice}")
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 2), (4, 4, 3), (3, 4, 4)])
+def test_every_launch_shape_matches_the_oracle(shape):
+    """Each register-cap instantiation of the particle kernels gives the
+    oracle's positions after 10 substeps, and the same gradient (the fused
+    adjoint included) as the default shape."""
+    w = W.cfg_small()
+    opts = mpm.make_options(checkpoint_every=16)
+
+    def grad(sim):
+        sim.reset()
+        sim.forward(40, record=True)
+        L, gx = sim.loss_mse(w.x0 + np.float32(0.002))
+        return sim.backward(dL_dx=gx)[0]
+
+    with mpm.simulation_from_workloads([w], opts) as sim:
+        sim.set_launch_shape(*shape)
+        assert tuple(sim.launch_shape().values()) == shape
+        sim.forward(10)
+        g = sim.get_state()
+        gm = grad(sim)
+        with pytest.raises(mpm.MpmError):
+            sim.set_launch_shape(5, 4, 3)
+    _compare(g, oracle_rollout(w, 10), 10, f"bed8k launch shape {shape}")
+    with mpm.simulation_from_workloads([w], opts) as ref:
+        gm0 = grad(ref)
+    print("gradient", gm[0], "default shape", gm0[0])
+    np.testing.assert_allclose(gm, gm0, rtol=2e-2, atol=1e-3 * np.abs(gm0).max())

@@ -189,3 +189,17 @@ def test_emd_matches_oracle(n_extra):
     same = np.all(np.abs(grad[owners] - go.astype(np.float32)) < 1e-4, axis=1)
     print("gradient rows equal to the oracle's:", same.mean())
     assert same.mean() > 0.9
+    # the GPU's map is one-to-one: each observed point's gradient row is the
+    # unit vector from its assigned target, which identifies that target
+    # (the targets are in general position); no target is used twice, and
+    # the assigned distances add up to the reported distance
+    Xd, Td = X.astype(np.float64), tgt.astype(np.float64)
+    rows = grad[owners].astype(np.float64)
+    diff = Xd[:, None, :] - Td[None, :, :]
+    dist = np.linalg.norm(diff, axis=2)
+    unit = diff / np.maximum(dist, 1e-30)[:, :, None]
+    err = np.linalg.norm(unit - rows[:, None, :], axis=2)
+    assigned = err.argmin(axis=1)
+    assert err[np.arange(len(assigned)), assigned].max() < 1e-3
+    assert np.unique(assigned).size == assigned.size, "a target is assigned twice"
+    assert abs(dist[np.arange(len(assigned)), assigned].sum() - L[0]) <= 1e-5 * L[0]

@@ -37,17 +37,23 @@ def test_material_gradient_is_invariant_under_scaling_E_and_rho():
 
 
 def test_batched_identification_reaches_five_percent_like_the_serial_loop():
+    """E and nu free from starts whose bulk modulus is 37% and 39% off: the
+    loop brings the identifiable quantity, K = E / (3 (1 - 2 nu)), within 5%
+    for both candidates, batched and serial, with the position loss falling."""
     w = W.cfg_small()
     truth = (w.E, w.nu, w.rho, w.phi_deg)
-    starts = [(1.4e5, w.nu, w.rho, w.phi_deg), (0.7e5, w.nu, w.rho, w.phi_deg)]
+    starts = [(1.4e5, 0.33, w.rho, w.phi_deg), (0.7e5, 0.27, w.rho, w.phi_deg)]
     grid = mpm.make_obs_grid((0.5, 0.5), 0.4, 40)
-    kw = dict(n_substeps=200, iterations=12, grid=grid, free=(True, False, False, False), line_search="mse")
+    kw = dict(n_substeps=200, iterations=30, grid=grid, free=(True, True, False, False), line_search="mse")
     b = sysid.identify(w, truth, starts, batched=True, **kw)
     s = sysid.identify(w, truth, starts, batched=False, **kw)
+    K_true = w.E / (3 * (1 - 2 * w.nu))
     for r, name in ((b, "batched"), (s, "serial")):
-        print(name, "E per iteration:", np.round(r.params[:, :, 0], -1).tolist())
+        K = r.params[:, :, 0] / (3 * (1 - 2 * r.params[:, :, 1]))
+        print(name, "K / K_true per iteration:", np.round(K / K_true, 3).tolist())
         print(name, "converged at", r.converged_at, "after", r.seconds_to_converge, "s")
         assert r.converged_at is not None, r.errors
+        assert (np.abs(K[-1] / K_true - 1) < 0.05).all()
         # the position loss fell on every candidate
         assert all(r.losses[-1][c] < r.losses[0][c] for c in range(len(starts)))
     # same arithmetic in both layouts: the same first update (later ones may

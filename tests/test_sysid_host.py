@@ -46,3 +46,26 @@ def test_identification_workload():
     s = W.cfg_sysid(n_substeps=300)
     b = np.asarray(s.traj.actions)
     assert np.isclose(-b[:15, 1].sum() / (15 * 10), -a[:75, 1].sum() / (75 * 10))
+
+
+def test_identifiable_quantities():
+    truth = np.array([1.2e5, 0.3, 1600.0, 32.0])
+    # E and nu free: the bulk modulus K = E / (3 (1 - 2 nu)); candidates on
+    # the curve of the true K have no error whatever E and nu are
+    K = 1.2e5 / (3 * 0.4)
+    nu = np.array([0.242, 0.3, 0.317])
+    on_curve = np.stack([3 * K * (1 - 2 * nu), nu, np.full(3, 1600.0), np.full(3, 32.0)], axis=1)
+    names, vals = sysid.identifiable(on_curve, (True, True, False, False))
+    assert names == ["K"] and np.allclose(vals[:, 0], K)
+    assert np.allclose(sysid._rel_error(on_curve, truth, np.array([True, True, False, False])), 0.0)
+    # off the curve: the relative error of K
+    off = np.array([[1.2e5 * 1.1, 0.3, 1600.0, 32.0]])
+    assert np.allclose(sysid._rel_error(off, truth, np.array([True, True, False, True])), 0.1)
+    # E and rho free: only E / rho; scaling both together is no error
+    scaled = np.array([[2.4e5, 0.3, 3200.0, 32.0]])
+    names, _ = sysid.identifiable(scaled, (True, False, True, False))
+    assert names == ["E/rho"]
+    assert np.allclose(sysid._rel_error(scaled, truth, np.array([True, False, True, False])), 0.0)
+    # nu alone free, rho alone free, phi
+    assert sysid.identifiable(truth[None, :], (False, True, False, True))[0] == ["nu", "phi"]
+    assert sysid.identifiable(truth[None, :], (False, False, True, False))[0] == ["rho"]
