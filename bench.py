@@ -251,9 +251,8 @@ def batched_vs_serial(n_inst: int, nsub: int, steps: int, sort_every: int):
     n_total = sum(w.n for w in ws)
     # the same checkpoint policy as the main leg, for the whole batch (each
     # instance alone then fits too): both arms use the same interval
-    nodes = sum(int(np.prod([-(-r // 4) * 4 for r in w.res])) for w in ws)
-    K = auto_checkpoint(nsub, 96 * n_total, 32 * nodes + nodes // 8 + 96 * n_total,
-                        torch.cuda.mem_get_info()[0])
+    nodes = sum(mpm.blocked_nodes(w.res) for w in ws)
+    K = auto_checkpoint(nsub, *mpm.record_bytes(n_total, nodes), torch.cuda.mem_get_info()[0])
     opts = mpm.make_options(checkpoint_every=K, sort_every=sort_every)
 
     def device_io(groups):
@@ -321,8 +320,7 @@ def full_rollout(nsub: int, steps: int):
 
     w = W.cfg_1m()
     N = w.n
-    nodes = int(np.prod([-(-r // 4) * 4 for r in w.res]))
-    slot_state, slot_grid = 96 * N, 32 * nodes + nodes // 8 + 96 * N
+    slot_state, slot_grid = mpm.record_bytes(N, mpm.blocked_nodes(w.res))
     K = auto_checkpoint(nsub, slot_state, slot_grid, torch.cuda.mem_get_info()[0])
     n_seg = -(-nsub // K)
     last = nsub - (n_seg - 1) * K
@@ -399,7 +397,7 @@ def sysid_leg(n_cand: int, nsub: int, iters: int):
 # --------------------------------------------------------------------------
 def auto_checkpoint(S: int, slot_state: int, slot_grid: int, free_bytes: int) -> int:
     """The largest checkpoint interval K <= S whose recorded segment (K + 1
-    states, K grids and SVD records) takes at most half the free device memory: with
+    state slots and K substep slots, mpm_record_bytes) takes at most half the free device memory: with
     K = S the backward reverses the recorded rollout without recomputing it."""
     budget = free_bytes // 2
     K = (budget - slot_state) // (slot_state + slot_grid)
@@ -426,10 +424,9 @@ def run_ours(args):
 
     w = W.cfg_1m()
     N, S = w.n, args.substeps
-    nodes = int(np.prod([-(-r // 4) * 4 for r in w.res]))
-    # per recorded substep: a state (96 B/particle), the grids (acc + vout +
-    # flags) and the SVD of the trial F (96 B/particle)
-    slot_state, slot_grid = 96 * N, 32 * nodes + nodes // 8 + 96 * N
+    # per recorded substep: a state, the grids (acc + vout + flags) and the
+    # SVD record of the trial F (the library's layout)
+    slot_state, slot_grid = mpm.record_bytes(N, mpm.blocked_nodes(w.res))
     K = args.checkpoint or auto_checkpoint(S, slot_state, slot_grid, torch.cuda.mem_get_info(local)[0])
     record_bytes = (K + 1) * slot_state + K * slot_grid
     stream = torch.cuda.Stream()

@@ -271,6 +271,15 @@ int mpm_get_action_grad(mpm_handle* h, int inst, double* dL_dactions, double* dL
  * sum_p rho V_p up to rounding. */
 int mpm_grid_mass(mpm_handle* h, double* mass);
 
+/* Device memory of a recorded forward, for choosing checkpoint_every: one
+ * state slot (x, v, C, F of every particle) and, per recorded substep, the
+ * substep slot (the SVD record of the trial F per particle, the grid
+ * accumulators, velocities and touched-block flags per node), for
+ * n_particles particles on n_nodes grid nodes (all instances; nodes counted
+ * in 4x4x4 blocks). A segment of K substeps holds K + 1 state slots and K
+ * substep slots. Host only; no handle or device needed. */
+int mpm_record_bytes(int64_t n_particles, int64_t n_nodes, int64_t* state_slot, int64_t* substep_slot);
+
 /* Launch shape of the particle kernels: the register cap each is compiled
  * for, as the minimum number of resident CTAs per SM, shape[0] k_p2g (3 or
  * 4), shape[1] k_g2p (3 or 4), shape[2] the fused adjoint k_p2g_g2p_bwd (2,

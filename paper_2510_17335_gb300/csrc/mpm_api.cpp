@@ -1472,6 +1472,14 @@ int mpm_get_action_grad(mpm_handle* h, int inst, double* dL_dactions, double* dL
     return MPM_OK;
 }
 
+int mpm_record_bytes(int64_t n_particles, int64_t n_nodes, int64_t* state_slot, int64_t* substep_slot) {
+    if (n_particles < 0 || n_nodes < 0 || !state_slot || !substep_slot) return MPM_ERR_INVALID_ARG;
+    *state_slot = n_particles * kStateComps * (int64_t)sizeof(float);
+    *substep_slot = n_particles * kSpecComps * (int64_t)sizeof(float) + n_nodes * 2 * (int64_t)sizeof(float4) +
+                    (int64_t)flag_ints((int)std::min<int64_t>(n_nodes / 64 + 1, 1LL << 30)) * (int64_t)sizeof(int);
+    return MPM_OK;
+}
+
 int mpm_set_launch_shape(mpm_handle* h, const int shape[3]) {
     if (!h || !shape) return MPM_ERR_INVALID_ARG;
     if (shape[0] < 3 || shape[0] > 4 || shape[1] < 3 || shape[1] > 4 || shape[2] < 2 || shape[2] > 4)

@@ -45,7 +45,7 @@
 namespace mpm {
 
 __device__ __forceinline__ float ld(const float* s, long long ncap, int comp, long long p) {
-    return s[comp * ncap + p];
+    return __ldcs(s + comp * ncap + p);
 }
 
 // a[i] through selects: where a stencil loop over i stays rolled (the P2G
@@ -139,34 +139,72 @@ __device__ __forceinline__ void load_trial(const InstDev& I, const StepArgs& a, 
 }
 
 // The recorded SVD of a particle's trial F (record mode): the adjoint
-// rebuilds the return mapping from it instead of redoing the SVD.
+// rebuilds the return mapping from it instead of redoing the SVD. U and V are
+// proper rotations and are kept as unit quaternions (w, x, y, z).
+// Rotation -> quaternion: the largest of 4w^2 = 1 + tr R, 4x^2 = 1 + R00 -
+// R11 - R22, ... is taken by its square root, the other three from the sums
+// and differences of symmetric off-diagonal pairs divided by it.
+__device__ __forceinline__ void rot_to_quat(const float (&R)[3][3], float (&q)[4]) {
+    const float tw = 1.0f + R[0][0] + R[1][1] + R[2][2];
+    const float tx = 1.0f + R[0][0] - R[1][1] - R[2][2];
+    const float ty = 1.0f - R[0][0] + R[1][1] - R[2][2];
+    const float tz = 1.0f - R[0][0] - R[1][1] + R[2][2];
+    const float a21 = R[2][1] - R[1][2], a02 = R[0][2] - R[2][0], a10 = R[1][0] - R[0][1];
+    const float s01 = R[0][1] + R[1][0], s02 = R[0][2] + R[2][0], s12 = R[1][2] + R[2][1];
+    const bool bw = tw >= tx && tw >= ty && tw >= tz;
+    const bool bx = !bw && tx >= ty && tx >= tz;
+    const bool by = !bw && !bx && ty >= tz;
+    const float t = bw ? tw : (bx ? tx : (by ? ty : tz));
+    const float r = 0.5f * rsqrtf(t);   // 1 / (2 sqrt t) = 1 / (4 q_big)
+    const float big = t * r;            // sqrt(t) / 2 = q_big
+    if (bw) { q[0] = big; q[1] = a21 * r; q[2] = a02 * r; q[3] = a10 * r; }
+    else if (bx) { q[0] = a21 * r; q[1] = big; q[2] = s01 * r; q[3] = s02 * r; }
+    else if (by) { q[0] = a02 * r; q[1] = s01 * r; q[2] = big; q[3] = s12 * r; }
+    else { q[0] = a10 * r; q[1] = s02 * r; q[2] = s12 * r; q[3] = big; }
+}
+
+__device__ __forceinline__ void quat_to_rot(const float (&q)[4], float (&R)[3][3]) {
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    // normalise away the rounding of the stored quaternion
+    const float n = rsqrtf(w * w + x * x + y * y + z * z);
+    const float s = 2.0f * n * n;
+    const float xx = s * x * x, yy = s * y * y, zz = s * z * z;
+    const float xy = s * x * y, xz = s * x * z, yz = s * y * z;
+    const float wx = s * w * x, wy = s * w * y, wz = s * w * z;
+    R[0][0] = 1.0f - yy - zz; R[0][1] = xy - wz; R[0][2] = xz + wy;
+    R[1][0] = xy + wz; R[1][1] = 1.0f - xx - zz; R[1][2] = yz - wx;
+    R[2][0] = xz - wy; R[2][1] = yz + wx; R[2][2] = 1.0f - xx - yy;
+}
+
 __device__ __forceinline__ void store_svd(float* spec, long long N, long long p, const Spectral<float>& S) {
+    float qu[4], qv[4];
+    rot_to_quat(S.U, qu);
+    rot_to_quat(S.V, qv);
 #pragma unroll
-    for (int r = 0; r < 3; r++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            spec[(3 * r + c) * N + p] = S.U[r][c];
-            spec[(9 + 3 * r + c) * N + p] = S.V[r][c];
-        }
+    for (int k = 0; k < 4; k++) {
+        __stcs(spec + k * N + p, qu[k]);
+        __stcs(spec + (4 + k) * N + p, qv[k]);
+    }
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        spec[(18 + k) * N + p] = S.s[k];
-        spec[(21 + k) * N + p] = S.h[k];
+        __stcs(spec + (8 + k) * N + p, S.s[k]);
+        __stcs(spec + (11 + k) * N + p, S.h[k]);
     }
 }
 
 __device__ __forceinline__ void load_svd(const float* spec, long long N, long long p, Spectral<float>& S) {
+    float qu[4], qv[4];
 #pragma unroll
-    for (int r = 0; r < 3; r++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            S.U[r][c] = spec[(3 * r + c) * N + p];
-            S.V[r][c] = spec[(9 + 3 * r + c) * N + p];
-        }
+    for (int k = 0; k < 4; k++) {
+        qu[k] = __ldcs(spec + k * N + p);
+        qv[k] = __ldcs(spec + (4 + k) * N + p);
+    }
+    quat_to_rot(qu, S.U);
+    quat_to_rot(qv, S.V);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        S.s[k] = spec[(18 + k) * N + p];
-        S.h[k] = spec[(21 + k) * N + p];
+        S.s[k] = __ldcs(spec + (8 + k) * N + p);
+        S.h[k] = __ldcs(spec + (11 + k) * N + p);
     }
 }
 
@@ -217,7 +255,7 @@ __device__ __forceinline__ void p2g_store_affine(const InstDev& I, const StepArg
     for (int r = 0; r < 3; r++)
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            a.sout[(kF + 3 * r + c) * N + p] = Fn[r][c];
+            __stcs(a.sout + (kF + 3 * r + c) * N + p, Fn[r][c]);
             finite = finite && isfinite(Fn[r][c]);
             A[r][c] = I.stress_scale * tau[r][c] + I.mp * C[r][c];
         }
@@ -484,15 +522,15 @@ __device__ __forceinline__ void g2p_particle(const InstDev& I, const StepArgs& a
     const float cscale = 4.0f * I.inv_dx;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        a.sout[(kX + k) * N + p] = xn[k];
-        a.sout[(kV + k) * N + p] = v[k];
+        __stcs(a.sout + (kX + k) * N + p, xn[k]);
+        __stcs(a.sout + (kV + k) * N + p, v[k]);
     }
 #pragma unroll
     for (int r = 0; r < 3; r++)
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             C[r][c] = cscale * B[r][c];
-            a.sout[(kC + 3 * r + c) * N + p] = C[r][c];
+            __stcs(a.sout + (kC + 3 * r + c) * N + p, C[r][c]);
         }
 }
 
@@ -820,7 +858,7 @@ __device__ __forceinline__ void unpark(const volatile float* sS, Spectral<float>
 // cheaper than keeping the value live across the gather)
 __device__ __forceinline__ float ld_again(const float* p) {
     float v;
-    asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    asm volatile("ld.global.cs.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
 

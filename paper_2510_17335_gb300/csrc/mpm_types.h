@@ -7,7 +7,7 @@ namespace mpm {
 constexpr int kChunk = 256;        // particles per CTA in particle kernels; instances are padded to it
 constexpr int kStateComps = 24;    // x 3, v 3, C 9, F 9 (structure of arrays)
 constexpr int kX = 0, kV = 3, kC = 6, kF = 15;
-constexpr int kSpecComps = 24;     // recorded SVD of the trial F: U 9, V 9, sigma 3, sigma^2 - 1 3
+constexpr int kSpecComps = 14;     // recorded SVD of the trial F: U and V as unit quaternions, sigma, sigma^2 - 1
 
 // status bits written by kernels
 constexpr int kStatusDomain = 1;

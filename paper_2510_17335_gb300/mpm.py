@@ -105,6 +105,8 @@ EXPORTS = {
     "mpm_set_substep": (_ip, [_vp, ctypes.c_int64]),
     "mpm_autotune": (_ip, [_vp, _ip, ctypes.POINTER(ctypes.c_int)]),
     "mpm_set_launch_shape": (_ip, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "mpm_record_bytes": (_ip, [ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_int64)]),
     "mpm_get_launch_shape": (_ip, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "mpm_profile": (_ip, [_vp, _ip]),
     "mpm_profile_read": (_ip, [_vp, _ip, _dp, ctypes.POINTER(ctypes.c_int64)]),
@@ -195,6 +197,20 @@ def loss_mse_noalloc(x, target, dL_dx=None, stream_ptr: int = 0) -> float:
         check(lib().mpm_loss_mse_noalloc(xp, tp, int(x.shape[0]), gp, ctypes.byref(L),
                                          ctypes.c_void_p(stream_ptr)), "mpm_loss_mse_noalloc")
     return L.value
+
+
+def record_bytes(n_particles: int, n_nodes: int) -> tuple[int, int]:
+    """mpm_record_bytes: (bytes of one state slot, bytes of one recorded
+    substep's slot) for n_particles particles on n_nodes grid nodes."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().mpm_record_bytes(int(n_particles), int(n_nodes), ctypes.byref(a), ctypes.byref(b)),
+          "mpm_record_bytes")
+    return a.value, b.value
+
+
+def blocked_nodes(res) -> int:
+    """Grid nodes of one instance as the library lays them out (4x4x4 blocks)."""
+    return int(np.prod([-(-int(r) // 4) * 4 for r in res]))
 
 
 def make_config(res, dx, dt, particle_volume, gravity=(0.0, -9.8, 0.0), bound=3, friction=0.5,

@@ -61,11 +61,11 @@ def _clamp(theta: np.ndarray) -> np.ndarray:
 
 def _auto_checkpoint(n_substeps: int, n_particles: int, n_nodes: int) -> int:
     """The largest checkpoint interval <= n_substeps whose recorded segment
-    (a state and the recorded SVD per particle, the grids per node, for every
-    substep of the segment) takes at most half the free device memory."""
+    (K + 1 state slots and K substep slots, mpm_record_bytes) takes at most
+    half the free device memory."""
     import torch
-    per_slot = 192 * n_particles + 32 * n_nodes + n_nodes // 8
-    k = (torch.cuda.mem_get_info()[0] // 2 - 96 * n_particles) // max(per_slot, 1)
+    state, sub = mpm.record_bytes(n_particles, n_nodes)
+    k = (torch.cuda.mem_get_info()[0] // 2 - state) // max(state + sub, 1)
     return int(max(1, min(n_substeps, k)))
 
 
@@ -148,7 +148,7 @@ def identify(w, truth: Sequence[float], starts: Sequence[Sequence[float]], n_sub
     theta = _clamp(np.asarray(starts, np.float64).reshape(-1, 4).copy())
     n_cand = theta.shape[0]
     free = np.asarray(free, bool)
-    nodes = int(np.prod([-(-r // 4) * 4 for r in w.res]))
+    nodes = mpm.blocked_nodes(w.res)
     k = checkpoint_every or _auto_checkpoint(n_substeps, n_cand * w.n, n_cand * nodes)
     opts = mpm.make_options(checkpoint_every=k, clip_grads=1, clip_value=clip_value)
 

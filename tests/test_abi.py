@@ -116,3 +116,17 @@ def test_noalloc_wrapper_rejects_bad_arrays_before_launch(monkeypatch):
     # right shapes, but host tensors: rejected as well
     with pytest.raises(ValueError, match="CUDA tensor"):
         mpm.loss_mse_noalloc(x, torch.zeros((8, 3)), torch.zeros((8, 3)))
+
+
+def test_record_bytes_follow_the_layout(L):
+    """mpm_record_bytes (host only): a state slot holds x, v, C, F (96 B a
+    particle); a substep slot the SVD record (U and V as quaternions, the
+    singular values and sigma^2 - 1: 56 B a particle), the accumulators and
+    velocities (32 B a node) and the touched-block flags and list."""
+    state, sub = mpm.record_bytes(1_048_576, 128 ** 3)
+    assert state == 96 * 1_048_576
+    blocks = 128 ** 3 // 64
+    assert sub == 56 * 1_048_576 + 32 * 128 ** 3 + 4 * (2 * (blocks + 1) + 1)
+    assert mpm.blocked_nodes((97, 64, 65)) == 100 * 64 * 68
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    assert L.mpm_record_bytes(-1, 10, ctypes.byref(a), ctypes.byref(b)) == -1
