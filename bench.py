@@ -396,12 +396,27 @@ def sysid_leg(n_cand: int, nsub: int, iters: int):
 # our implementation
 # --------------------------------------------------------------------------
 def auto_checkpoint(S: int, slot_state: int, slot_grid: int, free_bytes: int) -> int:
-    """The largest checkpoint interval K <= S whose recorded segment (K + 1
-    state slots and K substep slots, mpm_record_bytes) takes at most half the free device memory: with
-    K = S the backward reverses the recorded rollout without recomputing it."""
+    """The checkpoint interval for a recorded rollout of S substeps: at most
+    the largest K whose recorded segment (K + 1 state slots and K substep
+    slots, mpm_record_bytes) takes half the free device memory, and among
+    those the one that recomputes least. The backward reverses the last
+    segment from the record and recomputes every earlier one, so the
+    recomputed substeps are S minus the last segment's length; with K = S
+    nothing is recomputed."""
     budget = free_bytes // 2
-    K = (budget - slot_state) // (slot_state + slot_grid)
-    return int(max(1, min(S, K)))
+    k_max = int(max(1, min(S, (budget - slot_state) // (slot_state + slot_grid))))
+    return best_interval(S, k_max)
+
+
+def best_interval(S: int, k_max: int) -> int:
+    """The K <= k_max with the longest last segment (S - K (ceil(S / K) - 1)),
+    the larger K on ties."""
+    best, best_last = 1, 0
+    for K in range(1, k_max + 1):
+        last = S - K * (-(-S // K) - 1)
+        if last >= best_last:
+            best, best_last = K, last
+    return best
 
 
 def run_ours(args):

@@ -65,8 +65,15 @@ def _auto_checkpoint(n_substeps: int, n_particles: int, n_nodes: int) -> int:
     half the free device memory."""
     import torch
     state, sub = mpm.record_bytes(n_particles, n_nodes)
-    k = (torch.cuda.mem_get_info()[0] // 2 - state) // max(state + sub, 1)
-    return int(max(1, min(n_substeps, k)))
+    k_max = int(max(1, min(n_substeps, (torch.cuda.mem_get_info()[0] // 2 - state) // max(state + sub, 1))))
+    # among the intervals that fit, the one whose last segment (reversed
+    # without recomputation) is longest
+    best, best_last = 1, 0
+    for k in range(1, k_max + 1):
+        last = n_substeps - k * (-(-n_substeps // k) - 1)
+        if last >= best_last:
+            best, best_last = k, last
+    return best
 
 
 def identifiable(theta: np.ndarray, free) -> tuple[list, np.ndarray]:
