@@ -349,7 +349,13 @@ def full_rollout(nsub: int, steps: int):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     sim.close()
+    peak, peak_kind = measured_peaks()
+    gbs = (FWD_BYTES + BWD_BYTES) * N * nsub / (ms / 1e3) / 1e9
     return {"workload": "bed1m_grid128, the skill's whole rollout from the initial bed",
+            "roofline": {"bound": "hbm", "bytes_per_particle_substep": FWD_BYTES + BWD_BYTES,
+                         "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                         "peak_kind": f"{peak_kind} hbm_gbs",
+                         "note": "the method's bytes only: the recomputed substeps count as overhead"},
             "substeps": nsub, "checkpoint_every": K, "segments": n_seg, "recomputed_substeps": nsub - last,
             "value": N * nsub / (ms / 1e3), "unit": "particle-substeps/s", "ms_per_step": ms, "steps": steps,
             "finite_gradient": bool(np.isfinite(gm).all()),
