@@ -364,6 +364,34 @@ def test_autotune_restores_state_and_keeps_parity():
     _compare(g, ref, 10, f"bed8k after autotune {choice}")
 
 
+def test_autotune_failure_leaves_the_handle_as_it_was():
+    """A trial that fails (a particle leaves the domain within the trial
+    substeps) makes mpm_autotune return the error and restore the state, its
+    particle order, the substep counter, the options and the launch shape;
+    the handle then runs as before."""
+    res, dx = 16, 1.0 / 16
+    cfg = mpm.make_config((res,) * 3, dx, 1e-3, dx ** 3 / 8, gravity=(0, 0, 0), shovel_on=0)
+    x = np.array([[0.5, 0.5, 0.5], [0.5, 0.5, 13.0 * dx]], np.float32)
+    v = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 30.0]], np.float32)
+    with mpm.Simulation([cfg], [(1e5, 0.3, 1500.0, 30.0)], [x], mpm.make_options(sort_every=0)) as sim:
+        sim.set_state(x, v)
+        sim.set_launch_shape(3, 4, 2)
+        before = sim.get_state()
+        info0 = sim.info()
+        with pytest.raises(mpm.MpmError) as e:
+            sim.autotune(8)
+        assert e.value.code == -4
+        after = sim.get_state()
+        for k in before:
+            assert np.array_equal(before[k], after[k]), k
+        assert sim.launch_shape() == {"p2g": 3, "g2p": 4, "fused": 2}
+        info1 = sim.info()
+        assert info1["substep"] == info0["substep"] and info1["recorded"] == 0
+        # device memory held is what it was (the tuner's copies are released)
+        assert info1["device_bytes"] >= info0["device_bytes"]
+        sim.forward(1)   # one substep still runs (the particle is 3 cells from the wall)
+
+
 @pytest.mark.parametrize("shape", [(3, 3, 2), (4, 4, 3), (3, 4, 4)])
 def test_every_launch_shape_matches_the_oracle(shape):
     """Each register-cap instantiation of the particle kernels gives the
