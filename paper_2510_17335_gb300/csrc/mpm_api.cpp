@@ -1628,6 +1628,9 @@ int mpm_autotune(mpm_handle* h, int trial_substeps, int* chosen) {
         RK(g.save_state());
         CK(cudaEventCreate(&g.e0));
         CK(cudaEventCreate(&g.e1));
+        // every trial eager: a repeated call would otherwise be the one that
+        // captures a CUDA graph, and its timing would include the capture
+        h->opt.cuda_graphs = 0;
         int rc = MPM_OK;
         // 1. register caps: every kernel's candidates in the same trials
         // (timed per launch by the profiler), each kernel keeps its fastest
