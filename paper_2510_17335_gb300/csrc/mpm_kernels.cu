@@ -553,12 +553,17 @@ __global__ void __launch_bounds__(kChunk, MINB) k_g2p(StepArgs a) {
 // ---------------------------------------------------------------------------
 // Adjoint of the APIC gather for one particle: scatter W b into the grid
 // velocity adjoint with b = gvn + kap gC d (hoisted over the loops), and
-// gx += sum Wbar grad W; the terms of gx through d sum to -kap gC^T Sv with
-// Sv = sum W v_node (velocities of the grid vg).
+// gx += sum Wbar grad W (Wbar = v_node . b); the terms of gx through d sum
+// to -kap gC^T Sv with Sv = sum W v_node (velocities of the grid vg). The
+// sums of Wbar run over k first (per (i, j): Pw = sum_k wz Wbar, Pd =
+// sum_k wz' Wbar). KnownSv: the caller passes Sv, the particle's gathered
+// velocity, which the forward stored as the next state's v wherever the
+// particle contact left it alone; else Sv is summed here.
+template <bool KnownSv>
 __device__ __forceinline__ void g2p_bwd_scatter(const InstDev& I, const AdjArgs& A, const Stencil& st,
                                                 const int (&ox)[3], const int (&oy)[3], const int (&oz)[3],
                                                 const float4* vg, TileSmem* T, const float (&gvn)[3],
-                                                const float (&gC)[3][3], float (&gx)[3]) {
+                                                const float (&gC)[3][3], float (&gx)[3], const float (&Sv_in)[3]) {
     const float kap = 4.0f * I.inv_dx * I.inv_dx;
     float kgC[3][3];
 #pragma unroll
@@ -568,6 +573,9 @@ __device__ __forceinline__ void g2p_bwd_scatter(const InstDev& I, const AdjArgs&
     float Sv[3] = {0.f, 0.f, 0.f};
     float4* ga = A.gacc + I.node_off;
     const AxisX lx = axis_x(st, ox);
+    float dz[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) dz[k] = (float(k) - st.fx[2]) * I.dx;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         const float wx = lx.w[i], dwx = lx.dw[i], dxi = (float(i) - st.fx[0]) * I.dx;
@@ -577,41 +585,59 @@ __device__ __forceinline__ void g2p_bwd_scatter(const InstDev& I, const AdjArgs&
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             const float wy = st.w[1][j], dyj = (float(j) - st.fx[1]) * I.dx;
-            const float wxy = wx * wy, gwx = dwx * wy, gwy = wx * st.dw[1][j];
+            const float wxy = wx * wy;
             float bij[3];
 #pragma unroll
             for (int r = 0; r < 3; r++) bij[r] = fmaf(kgC[r][1], dyj, bi[r]);
+            float Pw = 0.f, Pd = 0.f, Tv[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                const float wz = st.w[2][k], dzk = (float(k) - st.fx[2]) * I.dx;
+                const float wz = st.w[2][k];
                 const float W = wxy * wz;
                 const float4 g = __ldg(vg + lx.o[i] + oy[j] + oz[k]);
                 float b[3];
 #pragma unroll
-                for (int r = 0; r < 3; r++) b[r] = fmaf(kgC[r][2], dzk, bij[r]);
+                for (int r = 0; r < 3; r++) b[r] = fmaf(kgC[r][2], dz[k], bij[r]);
                 const float4 contrib = make_float4(W * b[0], W * b[1], W * b[2], 0.f);
                 if (T) tile_add(*T, ga, lx.o[i] + oy[j] + oz[k], st, i, j, k, contrib, 3);
                 else atomicAdd(ga + lx.o[i] + oy[j] + oz[k], contrib);
                 const float Wbar = g.x * b[0] + g.y * b[1] + g.z * b[2];
-                gx[0] = fmaf(Wbar, gwx * wz, gx[0]);
-                gx[1] = fmaf(Wbar, gwy * wz, gx[1]);
-                gx[2] = fmaf(Wbar, wxy * st.dw[2][k], gx[2]);
-                Sv[0] = fmaf(W, g.x, Sv[0]);
-                Sv[1] = fmaf(W, g.y, Sv[1]);
-                Sv[2] = fmaf(W, g.z, Sv[2]);
+                Pw = fmaf(wz, Wbar, Pw);
+                Pd = fmaf(st.dw[2][k], Wbar, Pd);
+                if (!KnownSv) {
+                    Tv[0] = fmaf(wz, g.x, Tv[0]);
+                    Tv[1] = fmaf(wz, g.y, Tv[1]);
+                    Tv[2] = fmaf(wz, g.z, Tv[2]);
+                }
+            }
+            gx[0] = fmaf(dwx * wy, Pw, gx[0]);
+            gx[1] = fmaf(wx * st.dw[1][j], Pw, gx[1]);
+            gx[2] = fmaf(wxy, Pd, gx[2]);
+            if (!KnownSv) {
+#pragma unroll
+                for (int r = 0; r < 3; r++) Sv[r] = fmaf(wxy, Tv[r], Sv[r]);
             }
         }
+    }
+    if (KnownSv) {
+#pragma unroll
+        for (int r = 0; r < 3; r++) Sv[r] = Sv_in[r];
     }
 #pragma unroll
     for (int c = 0; c < 3; c++) gx[c] -= kgC[0][c] * Sv[0] + kgC[1][c] * Sv[1] + kgC[2][c] * Sv[2];
 }
 
+// Tiled: with the shared-memory scatter tile (option tile_scatter, launched
+// with sizeof(TileSmem) bytes of dynamic shared memory); the plain
+// instantiation carries neither its code nor its memory.
+template <bool Tiled>
 __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A) {
     wait_previous_grid();
-    __shared__ TileSmem T;
+    extern __shared__ __align__(16) unsigned char s_tile[];
     __shared__ InstDev sI;
     __shared__ float sfac[2];
     const StepArgs& a = A.f;
+    TileSmem* T = Tiled ? reinterpret_cast<TileSmem*>(s_tile) : nullptr;
     const int inst = a.chunk_inst[blockIdx.x];
     if (A.gscale && threadIdx.x == 0) {
         // regularisers of the x and v adjoints of state k+1 (Sec. III-E)
@@ -629,9 +655,7 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A)
     }
     Stencil st;
     make_stencil(I, x, st);
-    if (a.tile) tile_begin(T, active, st, kChunk);
-    else if (threadIdx.x == 0) T.tiled = 0;
-    if (!a.tile) __syncthreads();
+    if (Tiled) tile_begin(*T, active, st, kChunk);
     int ox[3], oy[3], oz[3];
     node_offsets(I, st, ox, oy, oz);
     const float4* vg = a.vout + I.node_off;
@@ -684,11 +708,12 @@ __global__ void __launch_bounds__(kChunk, MPM_MINB_G2P_BWD) k_g2p_bwd(AdjArgs A)
         for (int r = 0; r < 3; r++)
 #pragma unroll
             for (int c = 0; c < 3; c++) gC[r][c] = A.adj[(kC + 3 * r + c) * N + p];
-        g2p_bwd_scatter(I, A, st, ox, oy, oz, vg, &T, gvn, gC, gx);
+        const float none[3] = {0.f, 0.f, 0.f};
+        g2p_bwd_scatter<false>(I, A, st, ox, oy, oz, vg, T, gvn, gC, gx, none);
 #pragma unroll
         for (int k = 0; k < 3; k++) A.adj[(kX + k) * N + p] = gx[k];
     }
-    tile_flush(T, I, A.gacc, nullptr, 0, kChunk);
+    if (Tiled) tile_flush(*T, I, A.gacc, nullptr, 0, kChunk);
 }
 
 // adjoint of the grid update of one touched block gw (one warp)
@@ -879,8 +904,18 @@ __device__ __forceinline__ void p2g_bwd_gather(const InstDev& I, const AdjArgs& 
     // through d = x_node - x_p sum to -Am^T S1 with S1 = sum W mv-bar, and
     // gv, gmp follow from S1 and S0 = sum W m-bar after the loop. The grid
     // holds m-bar / fm and mv-bar / fv (fm = fv = 1 unless regularising).
+    // W and grad W factor per axis, so every sum runs over k first: per
+    // (i, j) Pw = sum_k wz Wbar, Pd = sum_k wz' Wbar, Tm = sum_k wz m-bar,
+    // T0 = sum_k wz mv-bar, T1 = sum_k wz dz mv-bar, then weighted by the
+    // x and y factors.
     float S0 = 0.f, S1[3] = {0.f, 0.f, 0.f};
     const float mpf = I.mp * fm;
+    float dz[3], wzd[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        dz[k] = (float(k) - st.fx[2]) * I.dx;
+        wzd[k] = st.w[2][k] * dz[k];
+    }
 #pragma unroll
     for (int r = 0; r < 3; r++)
 #pragma unroll
@@ -893,33 +928,39 @@ __device__ __forceinline__ void p2g_bwd_gather(const InstDev& I, const AdjArgs& 
         for (int r = 0; r < 3; r++) ai[r] = fmaf(Am[r][0], dxi, I.mp * v[r]);
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            const float wy = st.w[1][j], dyj = (float(j) - st.fx[1]) * I.dx;
-            const float wxy = wx * wy, gwx = dwx * wy, gwy = wx * st.dw[1][j];
+            const float dyj = (float(j) - st.fx[1]) * I.dx;
             float aij[3];
 #pragma unroll
             for (int r = 0; r < 3; r++) aij[r] = fmaf(Am[r][1], dyj, ai[r]);
+            float Pw = 0.f, Pd = 0.f, Tm = 0.f, T0[3] = {0.f, 0.f, 0.f}, T1[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                const float wz = st.w[2][k], dzk = (float(k) - st.fx[2]) * I.dx;
-                const float W = wxy * wz;
                 const float4 g = ga[lx.o[i] + oy[j] + oz[k]];
-                const float gm = g.x, gmv[3] = {g.y, g.z, g.w};
+                const float gmv[3] = {g.y, g.z, g.w};
                 float ma = 0.f;
 #pragma unroll
-                for (int r = 0; r < 3; r++) ma = fmaf(gmv[r], fmaf(Am[r][2], dzk, aij[r]), ma);
-                const float Wbar = fmaf(fv, ma, mpf * gm);
-                gx[0] = fmaf(Wbar, gwx * wz, gx[0]);
-                gx[1] = fmaf(Wbar, gwy * wz, gx[1]);
-                gx[2] = fmaf(Wbar, wxy * st.dw[2][k], gx[2]);
-                S0 = fmaf(W, gm, S0);
+                for (int r = 0; r < 3; r++) ma = fmaf(gmv[r], fmaf(Am[r][2], dz[k], aij[r]), ma);
+                const float Wbar = fmaf(mpf, g.x, fv * ma);
+                Pw = fmaf(st.w[2][k], Wbar, Pw);
+                Pd = fmaf(st.dw[2][k], Wbar, Pd);
+                Tm = fmaf(st.w[2][k], g.x, Tm);
 #pragma unroll
                 for (int r = 0; r < 3; r++) {
-                    const float Wg = W * gmv[r];
-                    S1[r] += Wg;
-                    gA[r][0] = fmaf(Wg, dxi, gA[r][0]);
-                    gA[r][1] = fmaf(Wg, dyj, gA[r][1]);
-                    gA[r][2] = fmaf(Wg, dzk, gA[r][2]);
+                    T0[r] = fmaf(st.w[2][k], gmv[r], T0[r]);
+                    T1[r] = fmaf(wzd[k], gmv[r], T1[r]);
                 }
+            }
+            const float wy = st.w[1][j], wxy = wx * wy, wxyi = wxy * dxi, wxyj = wxy * dyj;
+            gx[0] = fmaf(dwx * wy, Pw, gx[0]);
+            gx[1] = fmaf(wx * st.dw[1][j], Pw, gx[1]);
+            gx[2] = fmaf(wxy, Pd, gx[2]);
+            S0 = fmaf(wxy, Tm, S0);
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+                S1[r] = fmaf(wxy, T0[r], S1[r]);
+                gA[r][0] = fmaf(wxyi, T0[r], gA[r][0]);
+                gA[r][1] = fmaf(wxyj, T0[r], gA[r][1]);
+                gA[r][2] = fmaf(wxy, T1[r], gA[r][2]);
             }
         }
     }
@@ -1033,9 +1074,12 @@ __device__ __forceinline__ void p2g_bwd_factors(const AdjArgs& A, int inst, floa
 // of the fused adjoint): advection, particle contact (pose sums per warp when
 // warp_uniform, all lanes calling; else per thread), scatter into G.gacc with
 // global atomics, and the partial x-bar of the state before it into G.adj.
+// sk: the state after G's substep, whose v is the particle's gathered
+// velocity wherever the particle contact left it alone.
 __device__ __forceinline__ void g2p_bwd_particle(const InstDev& I, const AdjArgs& G, int inst, long long p,
                                                  bool active, bool warp_uniform, const float (&gx_in)[3],
-                                                 const float (&gv_in)[3], const float (&gC)[3][3]) {
+                                                 const float (&gv_in)[3], const float (&gC)[3][3],
+                                                 const float* sk) {
     const StepArgs& a = G.f;
     const long long N = a.ncap;
     float x[3] = {0.5f, 0.5f, 0.5f};
@@ -1048,9 +1092,10 @@ __device__ __forceinline__ void g2p_bwd_particle(const InstDev& I, const AdjArgs
     int ox[3], oy[3], oz[3];
     node_offsets(I, st, ox, oy, oz);
     const float4* vg = a.vout + I.node_off;
-    float gx[3], gvn[3];
+    float gx[3], gvn[3], Sv[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < 3; k++) {
+        if (active) Sv[k] = ld_again(sk + (kV + k) * N + p);
         gx[k] = a.clip > 0.f ? clipf(gx_in[k], a.clip) : gx_in[k];
         const float gv = a.clip > 0.f ? clipf(gv_in[k], a.clip) : gv_in[k];
         gvn[k] = gv + I.dt * gx[k];   // adjoint of the advection x' = x + dt v'
@@ -1079,6 +1124,7 @@ __device__ __forceinline__ void g2p_bwd_particle(const InstDev& I, const AdjArgs
                 gvn[0] = gvn[1] = gvn[2] = 0.f;
                 shovel_project_adj(I, P, cs, sn, x, v, g0, gvn, gq, gp);
                 gx[0] += gq[0]; gx[1] += gq[1]; gx[2] += gq[2];
+                Sv[0] = v[0]; Sv[1] = v[1]; Sv[2] = v[2];
             }
         }
         if (warp_uniform) {
@@ -1090,7 +1136,7 @@ __device__ __forceinline__ void g2p_bwd_particle(const InstDev& I, const AdjArgs
         }
     }
     if (active) {
-        g2p_bwd_scatter(I, G, st, ox, oy, oz, vg, nullptr, gvn, gC, gx);
+        g2p_bwd_scatter<true>(I, G, st, ox, oy, oz, vg, nullptr, gvn, gC, gx, Sv);
 #pragma unroll
         for (int k = 0; k < 3; k++) G.adj[(kX + k) * N + p] = gx[k];
     }
@@ -1176,7 +1222,7 @@ __device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A, const AdjArgs* G) 
     // parameter sums first: their registers are free for the G2P adjoint
     float gd[4] = {gmu, glam, galpha, gmp};
     block_reduce_add<4>(gd, A.gmat + 4 * inst, sred);
-    if (Fused) g2p_bwd_particle(I, *G, inst, p, go_on, true, gxk, gvk, gCk);
+    if (Fused) g2p_bwd_particle(I, *G, inst, p, go_on, true, gxk, gvk, gCk, a.sin);
     if (Reg) {
         __syncthreads();   // sred is reused
         block_stat<3>(A.gscale, st, A.pstat_out + 3 * inst, reinterpret_cast<float*>(sred));
@@ -1236,7 +1282,7 @@ __device__ __forceinline__ void p2g_bwd_fp64_all(const AdjArgs& A, const AdjArgs
         p2g_bwd_affine(I, A, p, gA, fac[0], gFn, gtau, gC, gmp);
         constitutive_adjoint_fp64(Ft, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, tau, gFt, gmu, glam, galpha);
         p2g_bwd_finish<!Fused>(I, A, p, gx, gv, gC, gFt, A.gscale, st);
-        if (Fused) g2p_bwd_particle(I, *G, inst, p, true, false, gx, gv, gC);
+        if (Fused) g2p_bwd_particle(I, *G, inst, p, true, false, gx, gv, gC, a.sin);
         if (A.gscale)
             for (int k = 0; k < 3; k++) {
                 if (!(st[k] > 0.0f)) continue;
@@ -1556,7 +1602,8 @@ static inline int grid_ctas(int n_blocks) { return (n_blocks * 32 + 255) / 256; 
 // (wait_previous_grid) until the previous grid has completed and its writes
 // are visible, so the stream order of the results is unchanged.
 template <typename... P, typename... A>
-static cudaError_t launch_pdl(void (*k)(P...), unsigned grid, unsigned block, cudaStream_t s, A&&... args) {
+static cudaError_t launch_pdl_smem(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                                   A&&... args) {
 #if MPM_PDL
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1564,15 +1611,20 @@ static cudaError_t launch_pdl(void (*k)(P...), unsigned grid, unsigned block, cu
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
 #else
-    k<<<grid, block, 0, s>>>(std::forward<A>(args)...);
+    k<<<grid, block, smem, s>>>(std::forward<A>(args)...);
     return cudaGetLastError();
 #endif
+}
+
+template <typename... P, typename... A>
+static cudaError_t launch_pdl(void (*k)(P...), unsigned grid, unsigned block, cudaStream_t s, A&&... args) {
+    return launch_pdl_smem(k, grid, block, 0, s, std::forward<A>(args)...);
 }
 
 // CTAs of the kernels that walk a block list: a warp per block up to one
@@ -1597,7 +1649,9 @@ cudaError_t launch_kernel(KernelId id, const AdjArgs& A, const LaunchShape& ls, 
         case KernelId::G2P:
             return p2g_minb(ls.g2p) == 3 ? launch_pdl(k_g2p<3>, a.n_chunks, kChunk, s, a)
                                          : launch_pdl(k_g2p<4>, a.n_chunks, kChunk, s, a);
-        case KernelId::G2PBwd: return launch_pdl(k_g2p_bwd, a.n_chunks, kChunk, s, A);
+        case KernelId::G2PBwd:
+            return a.tile ? launch_pdl_smem(k_g2p_bwd<true>, a.n_chunks, kChunk, sizeof(TileSmem), s, A)
+                          : launch_pdl(k_g2p_bwd<false>, a.n_chunks, kChunk, s, A);
         case KernelId::GridBwd: return launch_pdl(k_grid_bwd, list_ctas(a.n_blocks), 256, s, A);
         case KernelId::P2GBwd:
             if (!a.spec) return cudaErrorInvalidValue;   // needs the recorded SVD
