@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--substeps", type=int, default=100)
     ap.add_argument("--checkpoint", type=int, default=0,
-                    help="checkpoint interval K (0: the largest K <= substeps whose record fits half the free HBM)")
+                    help="checkpoint interval K (0: mpm.checkpoint_interval for the free HBM)")
     ap.add_argument("--start", type=int, default=600, help="substep of the rollout start state")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -276,7 +276,7 @@ def batched_vs_serial(n_inst: int, nsub: int, steps: int, sort_every: int):
     # the same checkpoint policy as the main leg, for the whole batch (each
     # instance alone then fits too): both arms use the same interval
     nodes = sum(mpm.blocked_nodes(w.res) for w in ws)
-    K = auto_checkpoint(nsub, *mpm.record_bytes(n_total, nodes), torch.cuda.mem_get_info()[0])
+    K = mpm.checkpoint_interval(nsub, n_total, nodes, torch.cuda.mem_get_info()[0])
     opts = mpm.make_options(checkpoint_every=K, sort_every=sort_every)
 
     def device_io(groups):
@@ -345,8 +345,9 @@ def full_rollout(nsub: int, steps: int):
     w = W.cfg_1m()
     N = w.n
     slot_state, slot_grid = mpm.record_bytes(N, mpm.blocked_nodes(w.res))
-    K = auto_checkpoint(nsub, slot_state, slot_grid, torch.cuda.mem_get_info()[0])
+    K = mpm.checkpoint_interval(nsub, N, mpm.blocked_nodes(w.res), torch.cuda.mem_get_info()[0])
     n_seg = -(-nsub // K)
+    record = (K + 1) * slot_state + K * slot_grid + n_seg * slot_state
     last = nsub - (n_seg - 1) * K
     stream = torch.cuda.Stream()
     sim = mpm.simulation_from_workloads([w], mpm.make_options(checkpoint_every=K))
@@ -381,6 +382,7 @@ def full_rollout(nsub: int, steps: int):
                          "peak_kind": f"{peak_kind} hbm_gbs",
                          "note": "the method's bytes only: the recomputed substeps count as overhead"},
             "substeps": nsub, "checkpoint_every": K, "segments": n_seg, "recomputed_substeps": nsub - last,
+            "record_bytes": record,
             "value": N * nsub / (ms / 1e3), "unit": "particle-substeps/s", "ms_per_step": ms, "steps": steps,
             "finite_gradient": bool(np.isfinite(gm).all()),
             "timing": "CUDA events on the library's stream, after 2 warm-up steps (allocation, graph capture)"}
@@ -425,30 +427,6 @@ def sysid_leg(n_cand: int, nsub: int, iters: int):
 # --------------------------------------------------------------------------
 # our implementation
 # --------------------------------------------------------------------------
-def auto_checkpoint(S: int, slot_state: int, slot_grid: int, free_bytes: int) -> int:
-    """The checkpoint interval for a recorded rollout of S substeps: at most
-    the largest K whose recorded segment (K + 1 state slots and K substep
-    slots, mpm_record_bytes) takes half the free device memory, and among
-    those the one that recomputes least. The backward reverses the last
-    segment from the record and recomputes every earlier one, so the
-    recomputed substeps are S minus the last segment's length; with K = S
-    nothing is recomputed."""
-    budget = free_bytes // 2
-    k_max = int(max(1, min(S, (budget - slot_state) // (slot_state + slot_grid))))
-    return best_interval(S, k_max)
-
-
-def best_interval(S: int, k_max: int) -> int:
-    """The K <= k_max with the longest last segment (S - K (ceil(S / K) - 1)),
-    the larger K on ties."""
-    best, best_last = 1, 0
-    for K in range(1, k_max + 1):
-        last = S - K * (-(-S // K) - 1)
-        if last >= best_last:
-            best, best_last = K, last
-    return best
-
-
 def run_ours(args):
     import numpy as np
     import torch
@@ -472,7 +450,7 @@ def run_ours(args):
     # per recorded substep: a state, the grids (acc + vout + flags) and the
     # SVD record of the trial F (the library's layout)
     slot_state, slot_grid = mpm.record_bytes(N, mpm.blocked_nodes(w.res))
-    K = args.checkpoint or auto_checkpoint(S, slot_state, slot_grid, torch.cuda.mem_get_info(local)[0])
+    K = args.checkpoint or mpm.checkpoint_interval(S, N, mpm.blocked_nodes(w.res), torch.cuda.mem_get_info(local)[0])
     record_bytes = (K + 1) * slot_state + K * slot_grid
     stream = torch.cuda.Stream()
     opts = mpm.make_options(checkpoint_every=K, tile_scatter=args.tile, sort_every=args.sort)

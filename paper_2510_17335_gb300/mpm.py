@@ -213,6 +213,42 @@ def blocked_nodes(res) -> int:
     return int(np.prod([-(-int(r) // 4) * 4 for r in res]))
 
 
+def best_interval(n_substeps: int, k_max: int) -> int:
+    """The checkpoint interval K <= k_max that recomputes least. The backward
+    reverses the last segment from its record and recomputes every earlier
+    segment once from its checkpoint, so n_substeps minus the last segment's
+    length (S - K (ceil(S / K) - 1)) substeps are recomputed; among the K
+    with the longest last segment, the largest."""
+    S = int(n_substeps)
+    best, best_last = 1, 0
+    for K in range(1, int(k_max) + 1):
+        last = S - K * (-(-S // K) - 1)
+        if last >= best_last:
+            best, best_last = K, last
+    return best
+
+
+def checkpoint_interval(n_substeps: int, n_particles: int, n_nodes: int, free_bytes: int,
+                        reserve: int | None = None) -> int:
+    """The checkpoint interval for a recorded rollout of n_substeps on
+    n_particles particles and n_nodes grid nodes (all instances): the K that
+    recomputes least (best_interval) among those whose recording fits in
+    free_bytes less a reserve: the segment's K + 1 state slots and K substep
+    slots (mpm_record_bytes) and one state slot per segment's checkpoint.
+    The reserve (default: the larger of 8 GiB and a sixteenth of free_bytes)
+    is left for the handle's working buffers and the caller's."""
+    S = int(n_substeps)
+    state, sub = record_bytes(n_particles, n_nodes)
+    if reserve is None:
+        reserve = max(8 << 30, int(free_bytes) // 16)
+    budget = int(free_bytes) - int(reserve)
+    k_max = 1
+    for K in range(1, S + 1):
+        if (K + 1) * state + K * sub + (-(-S // K)) * state <= budget:
+            k_max = K
+    return best_interval(S, k_max)
+
+
 def make_config(res, dx, dt, particle_volume, gravity=(0.0, -9.8, 0.0), bound=3, friction=0.5,
                 particle_collision=1, shovel_half=(0.01, 0.075, 0.1), shovel_on=1) -> mpm_config:
     c = mpm_config()

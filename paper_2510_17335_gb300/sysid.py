@@ -59,23 +59,6 @@ def _clamp(theta: np.ndarray) -> np.ndarray:
     return np.minimum(np.maximum(theta, lo), hi)
 
 
-def _auto_checkpoint(n_substeps: int, n_particles: int, n_nodes: int) -> int:
-    """The largest checkpoint interval <= n_substeps whose recorded segment
-    (K + 1 state slots and K substep slots, mpm_record_bytes) takes at most
-    half the free device memory."""
-    import torch
-    state, sub = mpm.record_bytes(n_particles, n_nodes)
-    k_max = int(max(1, min(n_substeps, (torch.cuda.mem_get_info()[0] // 2 - state) // max(state + sub, 1))))
-    # among the intervals that fit, the one whose last segment (reversed
-    # without recomputation) is longest
-    best, best_last = 1, 0
-    for k in range(1, k_max + 1):
-        last = n_substeps - k * (-(-n_substeps // k) - 1)
-        if last >= best_last:
-            best, best_last = k, last
-    return best
-
-
 def identifiable(theta: np.ndarray, free) -> tuple[list, np.ndarray]:
     """The quantities the final positions identify, for candidates theta
     [n, 4] (E, nu, rho, phi) with the given parameters free: names and
@@ -143,8 +126,8 @@ def identify(w, truth: Sequence[float], starts: Sequence[Sequence[float]], n_sub
     (the serial path, same arithmetic). line_search: "hmd" ranks the step
     multiples by the height-map distance to the target map (Sec. III-F),
     "mse" by the position loss the gradient descends. checkpoint_every 0:
-    the largest interval whose recorded segment fits half the free device
-    memory (the whole rollout when it fits). Returns the parameter
+    mpm.checkpoint_interval for the free device memory (the whole rollout
+    when it fits). Returns the parameter
     history and the wall clock to bring every candidate within `tol`
     relative error on the free parameters (None if it never did)."""
     if line_search not in ("hmd", "mse"):
@@ -156,7 +139,11 @@ def identify(w, truth: Sequence[float], starts: Sequence[Sequence[float]], n_sub
     n_cand = theta.shape[0]
     free = np.asarray(free, bool)
     nodes = mpm.blocked_nodes(w.res)
-    k = checkpoint_every or _auto_checkpoint(n_substeps, n_cand * w.n, n_cand * nodes)
+    if not checkpoint_every:
+        import torch
+        checkpoint_every = mpm.checkpoint_interval(n_substeps, n_cand * w.n, n_cand * nodes,
+                                                   torch.cuda.mem_get_info()[0])
+    k = checkpoint_every
     opts = mpm.make_options(checkpoint_every=k, clip_grads=1, clip_value=clip_value)
 
     # target cloud and height map from the hidden material

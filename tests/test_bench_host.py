@@ -15,21 +15,6 @@ def test_recorded_counters_are_keyed_by_the_hash():
     assert len(sha) == 16 and all(c in "0123456789abcdef" for c in sha)
 
 
-def test_checkpoint_interval_recomputes_least():
-    # 500 substeps with room for at most 70 per segment: 63 leaves a last
-    # segment of 59 (441 recomputed), 70 would leave 10 (490 recomputed)
-    assert bench.best_interval(500, 70) == 63
-    # the whole 2,000-substep rollout with room for 550: 500 (1,500 recomputed, not 1,650)
-    assert bench.best_interval(2000, 550) == 500
-    assert bench.best_interval(100, 100) == 100 and bench.best_interval(100, 1) == 1
-    # brute force: no interval that fits recomputes less
-    for S in (7, 100, 333):
-        for k_max in (1, 5, 40, S):
-            K = bench.best_interval(S, k_max)
-            rec = lambda k: S - (S - k * (-(-S // k) - 1))
-            assert K <= k_max and all(rec(K) <= rec(k) for k in range(1, k_max + 1))
-
-
 def test_recorded_counters_match_the_current_kernels():
     """profiles/kernel_counters.txt holds ncu counters of the dominant kernel
     for the kernel sources as they are (else the bench would report no
