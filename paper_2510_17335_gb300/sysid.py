@@ -140,7 +140,6 @@ def identify(w, truth: Sequence[float], starts: Sequence[Sequence[float]], n_sub
     free = np.asarray(free, bool)
     nodes = mpm.blocked_nodes(w.res)
     if not checkpoint_every:
-        import torch
         checkpoint_every = mpm.checkpoint_interval(n_substeps, n_cand * w.n, n_cand * nodes,
                                                    torch.cuda.mem_get_info()[0])
     k = checkpoint_every
