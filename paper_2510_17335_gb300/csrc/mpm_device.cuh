@@ -838,7 +838,7 @@ __device__ __forceinline__ void warp_reduce_add(float (&v)[NV], double* dst, boo
 // atomic. Otherwise (particles of the chunk far apart) the CTA scatters
 // straight into the global grid. The decision is uniform per CTA.
 // ---------------------------------------------------------------------------
-constexpr int kTileNodes = 1024;
+constexpr int kTileNodes = 512;
 
 struct TileSmem {
     float c[4][kTileNodes];   // the four accumulated components, SoA

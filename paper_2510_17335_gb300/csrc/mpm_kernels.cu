@@ -192,8 +192,10 @@ __device__ __forceinline__ void store_svd(float* spec, long long N, long long p,
     }
 }
 
-__device__ __forceinline__ void load_svd(const float* spec, long long N, long long p, Spectral<float>& S) {
-    float qu[4], qv[4];
+// the record's quaternions of U and V (qu, qv), the rotations and sigma,
+// sigma^2 - 1
+__device__ __forceinline__ void load_svd(const float* spec, long long N, long long p, Spectral<float>& S,
+                                         float (&qu)[4], float (&qv)[4]) {
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         qu[k] = __ldcs(spec + k * N + p);
@@ -822,19 +824,20 @@ __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
                           [&](int gw) { clear_block(a, A.clr_flags, A.clr_acc, A.clr_gacc, gw, lane); });
 }
 
-// spectral data parked in shared memory across the gather (37 words a thread)
-constexpr int kParked = 37;
+// Spectral data parked in shared memory across the gather (27 words a
+// thread): U and V as their unit quaternions from the record (rebuilt by
+// unpark exactly as load_svd built them), the rest of the return mapping.
+constexpr int kParked = 27;
 
-__device__ __forceinline__ void park(volatile float* sS, const Spectral<float>& S) {
+__device__ __forceinline__ void park(volatile float* sS, const float (&qu)[4], const float (&qv)[4],
+                                     const Spectral<float>& S) {
     const int t = threadIdx.x;
     int w = 0;
 #pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            sS[(w++) * kChunk + t] = S.U[a][b];
-            sS[(w++) * kChunk + t] = S.V[a][b];
-        }
+    for (int k = 0; k < 4; k++) {
+        sS[(w++) * kChunk + t] = qu[k];
+        sS[(w++) * kChunk + t] = qv[k];
+    }
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         sS[(w++) * kChunk + t] = S.s[k];
@@ -852,13 +855,14 @@ __device__ __forceinline__ void park(volatile float* sS, const Spectral<float>& 
 __device__ __forceinline__ void unpark(const volatile float* sS, Spectral<float>& S, float smin) {
     const int t = threadIdx.x;
     int w = 0;
+    float qu[4], qv[4];
 #pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            S.U[a][b] = sS[(w++) * kChunk + t];
-            S.V[a][b] = sS[(w++) * kChunk + t];
-        }
+    for (int k = 0; k < 4; k++) {
+        qu[k] = sS[(w++) * kChunk + t];
+        qv[k] = sS[(w++) * kChunk + t];
+    }
+    quat_to_rot(qu, S.U);
+    quat_to_rot(qv, S.V);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         S.s[k] = sS[(w++) * kChunk + t];
@@ -1185,12 +1189,13 @@ __device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A, const AdjArgs* G) 
         float Am[3][3];
         {
             Spectral<float> S;
-            load_svd(a.spec, N, p, S);
+            float qu[4], qv[4];
+            load_svd(a.spec, N, p, S, qu, qv);
             return_map<float>(S, I.mu, I.lam, I.beta, I.smin);
             fb = needs_fp64(S);
             float Fn[3][3], tau[3][3];
             spectral_outputs<float, float>(S, Fn, tau);
-            park(sS, S);
+            park(sS, qu, qv, S);
 #pragma unroll
             for (int r = 0; r < 3; r++)
 #pragma unroll
