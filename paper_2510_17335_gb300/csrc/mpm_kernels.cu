@@ -824,10 +824,12 @@ __global__ void __launch_bounds__(256) k_grid_bwd(AdjArgs A) {
                           [&](int gw) { clear_block(a, A.clr_flags, A.clr_acc, A.clr_gacc, gw, lane); });
 }
 
-// Spectral data parked in shared memory across the gather (27 words a
-// thread): U and V as their unit quaternions from the record (rebuilt by
-// unpark exactly as load_svd built them), the rest of the return mapping.
-constexpr int kParked = 27;
+// Spectral data parked in shared memory across the gather (14 words a
+// thread): the record as loaded (U and V as quaternions, sigma, sigma^2 - 1);
+// unpark rebuilds U and V and redoes the return mapping from the same
+// values (cheaper than parking its 23 results, whose shared memory the
+// unified L1 keeps).
+constexpr int kParked = 14;
 
 __device__ __forceinline__ void park(volatile float* sS, const float (&qu)[4], const float (&qv)[4],
                                      const Spectral<float>& S) {
@@ -841,18 +843,11 @@ __device__ __forceinline__ void park(volatile float* sS, const float (&qu)[4], c
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         sS[(w++) * kChunk + t] = S.s[k];
-        sS[(w++) * kChunk + t] = S.eps[k];
-        sS[(w++) * kChunk + t] = S.shat[k];
-        sS[(w++) * kChunk + t] = S.e[k];
-        sS[(w++) * kChunk + t] = S.t[k];
+        sS[(w++) * kChunk + t] = S.h[k];
     }
-    sS[(w++) * kChunk + t] = S.nh;
-    sS[(w++) * kChunk + t] = S.tr;
-    sS[(w++) * kChunk + t] = S.kappa;
-    sS[(w++) * kChunk + t] = __int_as_float(S.kase);
 }
 
-__device__ __forceinline__ void unpark(const volatile float* sS, Spectral<float>& S, float smin) {
+__device__ __forceinline__ void unpark(const volatile float* sS, Spectral<float>& S, const InstDev& I) {
     const int t = threadIdx.x;
     int w = 0;
     float qu[4], qv[4];
@@ -866,21 +861,9 @@ __device__ __forceinline__ void unpark(const volatile float* sS, Spectral<float>
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         S.s[k] = sS[(w++) * kChunk + t];
-        S.eps[k] = sS[(w++) * kChunk + t];
-        S.shat[k] = sS[(w++) * kChunk + t];
-        S.e[k] = sS[(w++) * kChunk + t];
-        S.t[k] = sS[(w++) * kChunk + t];
+        S.h[k] = sS[(w++) * kChunk + t];
     }
-    S.nh = sS[(w++) * kChunk + t];
-    S.tr = sS[(w++) * kChunk + t];
-    S.kappa = sS[(w++) * kChunk + t];
-    S.kase = __float_as_int(sS[(w++) * kChunk + t]);
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        S.deps[k] = S.s[k] > smin ? 1.0f / S.s[k] : 0.0f;
-        S.ehat[k] = S.eps[k] - S.tr * (1.0f / 3.0f);
-        S.h[k] = 0.0f;
-    }
+    return_map<float>(S, I.mu, I.lam, I.beta, I.smin);
 }
 
 // a load the compiler may not merge with an earlier one (re-reading is
@@ -1209,7 +1192,7 @@ __device__ __forceinline__ void p2g_bwd_cta(const AdjArgs& A, const AdjArgs* G) 
             float gFn[3][3], gtau[3][3], gC[3][3], gFt[3][3];
             p2g_bwd_affine(I, A, p, gA, Reg ? sfac[0] : 1.0f, gFn, gtau, gC, gmp);
             Spectral<float> S;
-            unpark(sS, S, I.smin);
+            unpark(sS, S, I);
             constitutive_adjoint_spectral<float>(S, I.mu, I.lam, I.alpha, I.beta, I.smin, gFn, gtau, gFt, gmu, glam,
                                                  galpha);
             p2g_bwd_finish<!Fused>(I, A, p, gx, gv, gC, gFt, Reg ? A.gscale : 0, st);
