@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--full-substeps", type=int, default=2000,
                     help="substeps of the whole-rollout leg (0: skip); the 1M bed's rollout is 2,000")
     ap.add_argument("--full-steps", type=int, default=2)
+    ap.add_argument("--rollout-250k", type=int, default=1,
+                    help="the 250k-particle differentiable rollout leg, 1,000 substeps (0: skip)")
     ap.add_argument("--batch-substeps", type=int, default=500, help="substeps of each fwd+bwd loop of the batched leg (the uneven-batch workload runs 500)")
     return ap.parse_args()
 
@@ -327,40 +329,40 @@ def batched_vs_serial(n_inst: int, nsub: int, steps: int, sort_every: int):
 
 
 # --------------------------------------------------------------------------
-# the whole rollout of the 1M bed: 2,000 substeps fwd+bwd with recomputation
+# whole recorded rollouts fwd+bwd with checkpoint recomputation
 # --------------------------------------------------------------------------
-def full_rollout(nsub: int, steps: int):
-    """fwd+bwd of the skill's whole rollout of the 1M bed from its initial
-    state: a recorded forward of nsub substeps (checkpoint interval K from the
-    free memory), the MSE loss and the backward, which reverses the last
-    segment from the record and recomputes every earlier one from its
-    checkpoint. Timed with CUDA events on the library's stream after two
+def rollout_leg(w, nsub: int, steps: int, K: int, target, material=None):
+    """fwd+bwd of a whole rollout of workload w from its initial state: a
+    recorded forward of nsub substeps with checkpoint interval K, the MSE
+    loss against target (host, [n, 3]) and the backward, which reverses the
+    last segment from the record and recomputes every earlier one from its
+    checkpoint. material: the (E, nu, rho, phi) the rollout runs with (None:
+    the workload's). Timed with CUDA events on the library's stream after two
     warm-up steps (allocation, CUDA-graph capture)."""
     import numpy as np
     import torch
 
     from paper_2510_17335_gb300 import mpm
-    from paper_2510_17335_gb300 import workloads as W
 
-    w = W.cfg_1m()
     N = w.n
     slot_state, slot_grid = mpm.record_bytes(N, mpm.blocked_nodes(w.res))
-    K = mpm.checkpoint_interval(nsub, N, mpm.blocked_nodes(w.res), torch.cuda.mem_get_info()[0])
     n_seg = -(-nsub // K)
     record = (K + 1) * slot_state + K * slot_grid + n_seg * slot_state
     last = nsub - (n_seg - 1) * K
     stream = torch.cuda.Stream()
     sim = mpm.simulation_from_workloads([w], mpm.make_options(checkpoint_every=K))
+    if material is not None:
+        sim.set_material(0, material)
     sim.set_stream(stream.cuda_stream)
     dev = torch.device("cuda", torch.cuda.current_device())
     with torch.cuda.stream(stream):
-        target = (torch.from_numpy(w.x0).to(dev) + torch.tensor([0.003, -0.002, 0.001], device=dev)).contiguous()
+        tgt = torch.from_numpy(np.ascontiguousarray(target, np.float32)).to(dev)
         dldx = torch.empty((N, 3), device=dev)
 
         def step():
             sim.reset()
             sim.forward(nsub, record=True)
-            sim.loss_mse(target, grad_out=dldx)
+            sim.loss_mse(tgt, grad_out=dldx)
             return sim.backward(dL_dx=dldx)
 
         for _ in range(2):
@@ -369,23 +371,69 @@ def full_rollout(nsub: int, steps: int):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            gm, _ = step()
+            gm, gt = step()
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     sim.close()
     peak, peak_kind = measured_peaks()
     gbs = (FWD_BYTES + BWD_BYTES) * N * nsub / (ms / 1e3) / 1e9
-    return {"workload": "bed1m_grid128, the skill's whole rollout from the initial bed",
-            "roofline": {"bound": "hbm", "bytes_per_particle_substep": FWD_BYTES + BWD_BYTES,
+    return {"roofline": {"bound": "hbm", "bytes_per_particle_substep": FWD_BYTES + BWD_BYTES,
                          "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
                          "peak_kind": f"{peak_kind} hbm_gbs",
                          "note": "the method's bytes only: the recomputed substeps count as overhead"},
             "substeps": nsub, "checkpoint_every": K, "segments": n_seg, "recomputed_substeps": nsub - last,
             "record_bytes": record,
             "value": N * nsub / (ms / 1e3), "unit": "particle-substeps/s", "ms_per_step": ms, "steps": steps,
-            "finite_gradient": bool(np.isfinite(gm).all()),
+            "finite_gradient": bool(np.isfinite(gm).all() and (gt is None or np.isfinite(gt).all())),
             "timing": "CUDA events on the library's stream, after 2 warm-up steps (allocation, graph capture)"}
+
+
+def full_rollout(nsub: int, steps: int):
+    """The skill's whole rollout of the 1M bed (2,000 substeps) with the
+    checkpoint interval the free memory allows, against a shifted copy of
+    the initial bed."""
+    import numpy as np
+    import torch
+
+    from paper_2510_17335_gb300 import mpm
+    from paper_2510_17335_gb300 import workloads as W
+
+    w = W.cfg_1m()
+    K = mpm.checkpoint_interval(nsub, w.n, mpm.blocked_nodes(w.res), torch.cuda.mem_get_info()[0])
+    target = w.x0 + np.array([0.003, -0.002, 0.001], np.float32)
+    return {"workload": "bed1m_grid128, the skill's whole rollout from the initial bed",
+            **rollout_leg(w, nsub, steps, K, target)}
+
+
+def rollout_250k(steps: int):
+    """The differentiable-rollout workload: 250,000 particles on 96^3, 1,000
+    substeps from the initial bed with the start material, MSE of the final
+    positions against the final positions of the ground-truth material (an
+    untimed forward), gradients of (E, nu, rho, phi) and the six skill
+    parameters; checkpoint every 50 substeps as the workload states, and
+    again with the interval the free memory allows."""
+    import torch
+
+    from paper_2510_17335_gb300 import mpm
+    from paper_2510_17335_gb300 import workloads as W
+
+    w = W.cfg_250k()
+    nsub = w.n_substeps
+    with mpm.simulation_from_workloads([w]) as ref:
+        ref.forward(nsub)
+        target = ref.get_state()["x"]
+    start = w.extra["start_material"]
+    k_work = int(w.extra["checkpoint_every"])
+    k_mem = mpm.checkpoint_interval(nsub, w.n, mpm.blocked_nodes(w.res), torch.cuda.mem_get_info()[0])
+    out = {"workload": "bed250k_grid96: 250,000 particles, 96^3 grid, 1,000 substeps, MSE against the "
+                       "ground-truth material's final positions, start material +20%",
+           **rollout_leg(w, nsub, steps, k_work, target, start)}
+    if k_mem != k_work:
+        m = rollout_leg(w, nsub, steps, k_mem, target, start)
+        out["memory_interval"] = {k: m[k] for k in ("checkpoint_every", "recomputed_substeps", "value",
+                                                     "ms_per_step", "record_bytes")}
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -609,6 +657,7 @@ def run_ours(args):
     # the other legs need the main leg's memory
     sim.close()
     full = full_rollout(args.full_substeps, args.full_steps) if args.full_substeps > 0 else None
+    r250 = rollout_250k(args.full_steps) if args.rollout_250k else None
     batch = None
     if args.batch > 0:
         batch = batched_vs_serial(args.batch, args.batch_substeps, 3, args.sort)
@@ -621,12 +670,17 @@ def run_ours(args):
         r, secs, desc = oracle_sample(w, 24, 40, args.start, cores)
         r1, secs1, desc1 = oracle_sample(w, 24, 40, args.start, 1)
         rs, ss = oracle_small_workload(cores)
+        w250 = W.cfg_250k()
+        r250c, s250c, _ = oracle_sample(w250, max(w250.res), 20, 0, cores)
         cpu = {"value": r, "unit": "particle-substeps/s", "cores": cores, "kind": "oracle", "sample": desc,
                "seconds": round(secs, 2),
                "single_thread": {"value": r1, "cores": 1, "seconds": round(secs1, 2), "sample": desc1},
                "small_workload": {"value": rs, "cores": cores, "seconds": round(ss, 2),
                                   "sample": "the whole 8,000-particle parity workload on its 32^3 grid, "
-                                            "200 substeps fwd+bwd"}}
+                                            "200 substeps fwd+bwd"},
+               "rollout_250k": {"value": r250c, "cores": cores, "seconds": round(s250c, 2),
+                                "sample": f"the whole {w250.n}-particle bed of the differentiable-rollout "
+                                          "workload on its 96^3 grid, its first 20 substeps fwd+bwd"}}
     line = {
         "metric": "particle-substeps/s (fwd+bwd)", "value": value, "unit": "particle-substeps/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -641,6 +695,7 @@ def run_ours(args):
         "fwd_value": fwd_value, "fwd_ms_per_step": fms / args.steps,
         "roofline": roof, "roofline_step": roof_step, "alu": alu, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "full_rollout": full,
+        "rollout_250k": r250,
         "batched_vs_serial": batch,
         **({"sysid": sid} if sid is not None else {}),
         "kernels": kernels, "clocks": clk,
