@@ -103,27 +103,34 @@ def _rel_error(theta: np.ndarray, truth: np.ndarray, free: np.ndarray) -> np.nda
 
 class _Group:
     """Handles of one group of candidates: the gradient handle (one instance
-    per candidate) and the line-search handle (one instance per candidate and
-    step multiple)."""
+    per candidate) and the line-search handles, which hold one instance per
+    candidate and step multiple: all in one handle, or (split) one handle
+    each."""
 
-    def __init__(self, w, n_cand: int, n_substeps: int, options):
+    def __init__(self, w, n_cand: int, n_substeps: int, options, split: bool = False):
         self.n_cand = n_cand
         self.grad = mpm.simulation_from_workloads([w] * n_cand, options)
-        self.ls = mpm.simulation_from_workloads([w] * (n_cand * len(ALPHAS)), options)
+        n_ls = n_cand * len(ALPHAS)
+        self.ls = ([mpm.simulation_from_workloads([w], options) for _ in range(n_ls)] if split
+                   else [mpm.simulation_from_workloads([w] * n_ls, options)])
         self.n_substeps = n_substeps
 
     def close(self):
         self.grad.close()
-        self.ls.close()
+        for h in self.ls:
+            h.close()
 
 
 def identify(w, truth: Sequence[float], starts: Sequence[Sequence[float]], n_substeps: int, iterations: int,
              grid: "mpm.mpm_obs_grid", free=(True, True, False, True), tol: float = 0.05, batched: bool = True,
-             checkpoint_every: int = 0, clip_value: float = 1e4, line_search: str = "hmd") -> SysIdResult:
+             checkpoint_every: int = 0, clip_value: float = 1e4, line_search: str = "hmd",
+             per_instance: bool = False) -> SysIdResult:
     """Identify the material of workload w from the final state of a rollout
     with the hidden material `truth`, starting every candidate from
     starts[c]; batched: all candidates in one handle, else one handle each
-    (the serial path, same arithmetic). line_search: "hmd" ranks the step
+    (the serial path, same arithmetic), whose line search runs the step
+    multiples together, or with per_instance each on a handle of its own
+    (every instance launched alone). line_search: "hmd" ranks the step
     multiples by the height-map distance to the target map (Sec. III-F),
     "mse" by the position loss the gradient descends. checkpoint_every 0:
     mpm.checkpoint_interval for the free device memory (the whole rollout
@@ -152,14 +159,17 @@ def identify(w, truth: Sequence[float], starts: Sequence[Sequence[float]], n_sub
         x_target = ref.get_state()["x"]
         map_target = ref.height_map(grid)[0]
 
-    groups = [_Group(w, n_cand, n_substeps, opts)] if batched else [_Group(w, 1, n_substeps, opts)
-                                                                    for _ in range(n_cand)]
+    split = per_instance and not batched
+    groups = ([_Group(w, n_cand, n_substeps, opts)] if batched
+              else [_Group(w, 1, n_substeps, opts, split) for _ in range(n_cand)])
     members = [list(range(n_cand))] if batched else [[c] for c in range(n_cand)]
     io = []
     for g, mem in zip(groups, members):
         tgt = torch.from_numpy(np.tile(x_target, (len(mem), 1))).cuda()
-        ls_tgt = torch.from_numpy(np.tile(x_target, (len(mem) * len(ALPHAS), 1))).cuda()
-        io.append((tgt, torch.empty_like(tgt), np.tile(map_target, (len(mem) * len(ALPHAS), 1, 1)), ls_tgt))
+        # per line-search handle: its instances' target maps and clouds
+        ls_io = [(np.tile(map_target, (h.n_inst, 1, 1)), torch.from_numpy(np.tile(x_target, (h.n_inst, 1))).cuda())
+                 for h in g.ls]
+        io.append((tgt, torch.empty_like(tgt), ls_io))
 
     res = SysIdResult(params=np.zeros((iterations + 1, n_cand, 4)))
     res.params[0] = theta
@@ -168,7 +178,7 @@ def identify(w, truth: Sequence[float], starts: Sequence[Sequence[float]], n_sub
     try:
         for it in range(iterations):
             L_all = np.zeros(n_cand)
-            for g, mem, (tgt, dl, maps, ls_tgt) in zip(groups, members, io):
+            for g, mem, (tgt, dl, ls_io) in zip(groups, members, io):
                 # gradient of the position loss at the current candidates
                 for k, c in enumerate(mem):
                     g.grad.set_material(k, theta[c])
@@ -181,17 +191,23 @@ def identify(w, truth: Sequence[float], starts: Sequence[Sequence[float]], n_sub
                 gm = np.where(free[None, :], gm, 0.0)
                 msq[mem] = BETA * msq[mem] + (1.0 - BETA) * gm * gm
                 step = np.asarray(STEP)[None, :] * gm / (np.sqrt(msq[mem]) + 1e-30)
-                # line search: every candidate at every multiple, one forward
+                # line search: every candidate at every multiple (candidate-
+                # major), one forward per line-search handle
                 trial = np.stack([_clamp(theta[mem] - a * step) for a in ALPHAS], axis=1)   # [m, 5, 4]
-                for k in range(len(mem)):
-                    for j in range(len(ALPHAS)):
-                        g.ls.set_material(k * len(ALPHAS) + j, trial[k, j])
-                g.ls.reset()
-                g.ls.forward(n_substeps)
-                if line_search == "hmd":
-                    score, _ = g.ls.loss_hmd(grid, maps, want_grad=False)
-                else:
-                    score, _ = g.ls.loss_mse(ls_tgt, want_grad=False)
+                flat = trial.reshape(-1, 4)
+                scores, i0 = [], 0
+                for h, (maps, ls_tgt) in zip(g.ls, ls_io):
+                    for k in range(h.n_inst):
+                        h.set_material(k, flat[i0 + k])
+                    h.reset()
+                    h.forward(n_substeps)
+                    if line_search == "hmd":
+                        sc, _ = h.loss_hmd(grid, maps, want_grad=False)
+                    else:
+                        sc, _ = h.loss_mse(ls_tgt, want_grad=False)
+                    scores.append(np.asarray(sc))
+                    i0 += h.n_inst
+                score = np.concatenate(scores)
                 best = score.reshape(len(mem), len(ALPHAS)).argmin(axis=1)   # ties: the smaller multiple
                 theta[mem] = trial[np.arange(len(mem)), best]
             res.params[it + 1] = theta

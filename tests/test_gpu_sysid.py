@@ -59,3 +59,17 @@ def test_batched_identification_reaches_five_percent_like_the_serial_loop():
     # same arithmetic in both layouts: the same first update (later ones may
     # part where two step multiples score within summation-order noise)
     assert np.allclose(b.params[1], s.params[1], rtol=1e-3), (b.params[1], s.params[1])
+
+
+def test_per_instance_serial_loop_takes_the_same_steps():
+    """The fully serial layout (every line-search instance on a handle of its
+    own) runs the same arithmetic as the per-candidate one: the same updates
+    for the first iterations, up to the order of float sums."""
+    w = W.cfg_small()
+    truth = (w.E, w.nu, w.rho, w.phi_deg)
+    starts = [(1.4e5, 0.33, w.rho, w.phi_deg), (0.7e5, 0.27, w.rho, w.phi_deg)]
+    grid = mpm.make_obs_grid((0.5, 0.5), 0.4, 40)
+    kw = dict(n_substeps=120, iterations=2, grid=grid, free=(True, True, False, False), line_search="mse")
+    s = sysid.identify(w, truth, starts, batched=False, **kw)
+    p = sysid.identify(w, truth, starts, batched=False, per_instance=True, **kw)
+    assert np.allclose(s.params[1], p.params[1], rtol=1e-3), (s.params[1], p.params[1])
