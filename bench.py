@@ -659,14 +659,16 @@ def run_ours(args):
                  "fwd_bytes_per_particle_substep": FWD_BYTES,
                  "fwd_frac": round(FWD_BYTES * N * S * args.steps / (fms / 1e3) / 1e9 / peak, 4),
                  "peak_kind": f"{peak_kind} hbm_gbs"}
-    # the other legs need the main leg's memory
+    # the other legs need the main leg's memory; they characterise one GPU,
+    # so a multi-rank run (replicas) skips them
     sim.close()
-    full = full_rollout(args.full_substeps, args.full_steps) if args.full_substeps > 0 else None
-    r250 = rollout_250k(args.full_steps) if args.rollout_250k else None
+    one = ws == 1
+    full = full_rollout(args.full_substeps, args.full_steps) if one and args.full_substeps > 0 else None
+    r250 = rollout_250k(args.full_steps) if one and args.rollout_250k else None
     batch = None
-    if args.batch > 0:
+    if one and args.batch > 0:
         batch = batched_vs_serial(args.batch, args.batch_substeps, 3, args.sort)
-    sid = sysid_leg(args.sysid, args.sysid_substeps, args.sysid_iters) if args.sysid > 0 else None
+    sid = sysid_leg(args.sysid, args.sysid_substeps, args.sysid_iters) if one and args.sysid > 0 else None
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         # the oracle on every host core (OpenMP), and its plain serial loops
