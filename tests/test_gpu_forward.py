@@ -327,6 +327,49 @@ def test_full_size_sampled_substep():
     print(f"full-size sampled substep: worst |dx| {worst:.2e}")
 
 
+def test_full_size_batch_sampled_substep():
+    """The 64 uneven instances (20k-192k particles, 64^3-96^3 grids, each with
+    its own material and shovel) in one handle, as the bench's batched leg
+    runs them: after 20 GPU substeps, one more GPU substep is compared, for
+    sampled particles of the smallest, the largest and two other instances,
+    with the oracle run on each sample's neighbourhood in its own instance;
+    every instance keeps its mass."""
+    ws = W.batch_uneven(64)
+    counts = [w.n for w in ws]
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    with mpm.simulation_from_workloads(ws) as sim:
+        sim.forward(20)
+        s0 = sim.get_state()
+        sim.forward(1)
+        s1 = sim.get_state()
+        gm = sim.grid_mass()
+    for i, w in enumerate(ws):
+        assert np.isclose(gm[i], w.n * w.rho * w.vol, rtol=1e-6), i
+    rng = np.random.default_rng(9)
+    picks = {int(np.argmin(counts)), int(np.argmax(counts))}
+    picks |= set(int(i) for i in rng.choice(len(ws), 2, replace=False))
+    worst = 0.0
+    for i in sorted(picks):
+        w = ws[i]
+        sl = slice(offs[i], offs[i + 1])
+        x0 = s0["x"][sl]
+        p = oracle_params(w)
+        poses = oracle_poses(w, 21)[20:21]
+        base = np.floor(x0.astype(np.float64) / w.dx - 0.5).astype(np.int64)
+        for q in rng.choice(w.n, 6, replace=False):
+            nb = np.where(np.abs(base - base[q]).max(1) <= 2)[0]
+            j = int(np.where(nb == q)[0][0])
+            st, r = oracle.rollout(p, x0[nb].astype(np.float64), s0["v"][sl][nb], s0["C"][sl][nb].reshape(-1, 9),
+                                   s0["F"][sl][nb].reshape(-1, 9), poses)
+            assert st == 0
+            dx_ = np.abs(s1["x"][sl][q] - r["x"][j]).max()
+            dF_ = np.abs(s1["F"][sl][q] - r["F"][j]).max()
+            worst = max(worst, dx_)
+            assert dx_ < 1e-6, (i, q, dx_)
+            assert dF_ < 1e-5, (i, q, dF_)
+    print(f"full-size batch sampled substep: instances {sorted(picks)}, worst |dx| {worst:.2e}")
+
+
 def test_sorted_scrambled_order_matches_oracle():
     """Particles given in a random order and re-sorted by grid block every 3
     substeps: the state (read back in the caller's order) still matches the
