@@ -386,6 +386,61 @@ def test_full_size_adjoint_against_oracle():
     assert np.quantile(e, 0.99) < BAR
 
 
+def test_full_size_batch_adjoint_against_oracle():
+    """The 64 uneven instances (20k-192k particles, 64^3-96^3 grids, each
+    with its own material and shovel) in one handle, as the bench's batched
+    leg runs them: a 4-substep recorded rollout from their state after 200
+    substeps and its backward under each instance's MSE loss against a
+    shifted target; every instance's loss, material gradient and sampled
+    state adjoints against the oracle's FP64 adjoint of that instance (the
+    threaded oracle, which its own tests pin to its serial loops). The beds
+    have settled by then: in the first substeps from the unstrained lattice
+    the trace of the log strain sits at zero, where the return mapping's
+    apex test (Eqs. (6)-(7)) flips on rounding and the nu and phi gradients
+    follow the rounding, not the method."""
+    import os
+    ws = W.batch_uneven(64)
+    offs = np.concatenate([[0], np.cumsum([w.n for w in ws])])
+    start, nsub = 200, 4
+    with mpm.simulation_from_workloads(ws) as sim:
+        sim.forward(start)
+        s0 = sim.get_state()
+    target = np.concatenate([w.x0 + np.array([0.003, -0.002, 0.001], np.float32) for w in ws]).astype(np.float32)
+    with mpm.simulation_from_workloads(ws, mpm.make_options(checkpoint_every=2)) as sim:
+        sim.set_substep(start)
+        sim.set_state(s0["x"], s0["v"], s0["C"], s0["F"])
+        sim.forward(nsub, record=True)
+        L, gxs = sim.loss_mse(target)
+        gm, _ = sim.backward(dL_dx=gxs)
+        gs = sim.state_grad()
+    rng = np.random.default_rng(23)
+    oracle.set_threads(os.cpu_count() or 1)
+    worst_m, worst_x = 0.0, 0.0
+    try:
+        for i, w in enumerate(ws):
+            sl = slice(offs[i], offs[i + 1])
+            n = w.n
+            x, v, C, F = [np.asarray(s0[k][sl], np.float64).reshape(n, -1) for k in ("x", "v", "C", "F")]
+            p = oracle_params(w)
+            poses = oracle_poses(w, start + nsub)[start:]
+            st, r = oracle.rollout(p, x, v, C, F, poses)
+            assert st == 0
+            Lr, gx = oracle.mse_loss(r["x"], target[sl])
+            assert np.isclose(L[i], Lr, rtol=1e-5), (i, L[i], Lr)
+            st, g = oracle.rollout_adjoint(p, x, v, C, F, poses, gx=gx)
+            assert st == 0
+            em = rel_err(gm[i], g["material"]).max()
+            worst_m = max(worst_m, em)
+            assert em < BAR, (i, gm[i], g["material"])
+            idx = rng.choice(n, min(n, 512), replace=False)
+            ex = np.quantile(rel_err(gs["x"][sl][idx], g["x"][idx]), 0.99)
+            worst_x = max(worst_x, ex)
+            assert ex < BAR, (i, ex)
+    finally:
+        oracle.set_threads(1)
+    print(f"full-size batch adjoint: worst material rel err {worst_m:.2e}, worst x-bar p99 {worst_x:.2e}")
+
+
 def test_sorted_segments_give_the_same_gradients():
     """Sorting the particles at every segment start (the backward undoes
     each permutation on the adjoint) changes only the order of the float
